@@ -1,0 +1,810 @@
+/*
+ * FP64 reference ("oracle") for the two-species D2Q9 multiple-relaxation-time
+ * lattice Boltzmann model of Wang, Xu & Guo, "Lattice Boltzmann simulation of
+ * separation phenomenon in a binary gaseous flow through a microchannel"
+ * (arXiv:1603.08221), Sec. 3.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain, obviously-correct
+ * restatement of the method that the CUDA library is checked against.  Only
+ * the test-suite, the smoke check and the benchmark's CPU-baseline leg load
+ * it; the product library never links, calls or falls back to it, and the two
+ * share no source, header, table or helper.
+ *
+ * Every time step follows the paper's evolution equation (Eq. MRT) in push
+ * form, in this order:
+ *   1. moments and relaxation times of the pre-collision state (Eqs. rhou,
+ *      EQFrb, taos, EQFrsp, taoq, A12);
+ *   2. MRT collision Omega = -M^{-1} S (m - m^eq) (Eqs. MR, m, S, feq) with
+ *      dense 9x9 products and M^{-1} from Gauss-Jordan elimination;
+ *   3. extrapolation-correction ghost columns at inlet and outlet
+ *      (Eqs. rho1, rho2), built from the post-collision columns 1, 2;
+ *   4. push streaming;
+ *   5. diffuse-bounce-back on the unknown populations of rows 1 and N
+ *      (Eqs. bot, bot2, R).
+ *
+ * Units: lattice units with dx = dt = c = 1, c_s^2 = k_B T / m_min = 1/3 and
+ * molecular masses normalised by m_min, so k_B T = 1/3, rho_s = n_s * m_s and
+ * p = n k_B T.  The outlet number density is 1 and H = N.
+ *
+ * Readings where the paper is silent, ambiguous or garbled (each also listed
+ * in the design notes):
+ *  - velocity order is the one implied by the rows of M (c1=(1,0), c2=(0,1),
+ *    c3=(-1,0), c4=(0,-1), c5=(1,1), c6=(-1,1), c7=(-1,-1), c8=(1,-1));
+ *  - the collision operator carries a minus sign (Eq. MR prints none);
+ *  - viscosities mu_s, mu are not given: mu is the constant that gives
+ *    lambda = Kn_out * H at the outlet composition and pressure, and
+ *    mu_s = mu_ratio_s * mu;
+ *  - lambda_s uses the partial pressure p_s = x_s p;
+ *  - the slip coefficient c_m (Eq. cm) has undefined symbols; it is an input
+ *    c_m0 at alpha = 1, scaled by (2 - alpha)/alpha;
+ *  - r_s uses the first printed form of Eq. R with the wall node's m_x taken
+ *    from the state being reflected; both species share it;
+ *  - the wall equilibrium has u_w = 0 and the wall density that makes the
+ *    normal flux of each species vanish;
+ *  - tau_q (Eq. taoq) uses the derivative tau'_s(0) in its last term; it is
+ *    computed per column from the wall node's state and used in the half of
+ *    the column nearer that wall;
+ *  - rho_s,in = p_s,in / (s_s c_s^2) (consistent with Eq. P and f^eq);
+ *  - ghost columns extrapolate all nine post-collision populations and are
+ *    scaled by the density-correction factor of Eq. rho2.
+ *
+ * parity unpinned: the absolute values of CL, C~_l and the velocity profiles
+ * cannot be compared with the paper (its figures are not available and c_m,
+ * mu_s are not given); the tests pin this file against invariants, closed
+ * forms and independent special cases instead.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define Q 9
+
+/* D2Q9 velocities in the order implied by the rows of M (Eq. m). */
+static const int CX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+/* Weights below Eq. feq. */
+static const double WGT[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
+                              1.0 / 9.0,  1.0 / 9.0,  1.0 / 36.0,
+                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+/* Transform matrix M, Eq. (m), rows rho, e, eps, j_x, q_x, j_y, q_y, p_xx,
+ * p_xy. */
+static const double MM[Q][Q] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1},       {-4, -1, -1, -1, -1, 2, 2, 2, 2},
+    {4, -2, -2, -2, -2, 1, 1, 1, 1},   {0, 1, 0, -1, 0, 1, -1, -1, 1},
+    {0, -2, 0, 2, 0, 1, -1, -1, 1},    {0, 0, 1, 0, -1, 1, 1, -1, -1},
+    {0, 0, -2, 0, 2, 1, 1, -1, -1},    {0, 1, -1, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+
+static const double PI = 3.14159265358979323846;
+static const double EULER_GAMMA = 0.57721566490153286061;
+
+typedef struct {
+  double m_a, m_b;      /* molecular masses (any unit) */
+  double C_l;           /* light-species mole fraction at the inlet */
+  double C_l_out;       /* at the outlet; < 0 means equal to C_l */
+  double theta;         /* P_in / P_out */
+  double Kn_out;        /* lambda_out / H */
+  int N;                /* lattice cells across H */
+  int N_x;              /* lattice columns along the channel */
+  double accommodation; /* alpha of Eq. A12 (uniform default) */
+  double c_m0;          /* slip coefficient at alpha = 1 */
+  double tau_rho, tau_e, tau_eps;
+  double mu_ratio_a, mu_ratio_b;
+  int x_periodic; /* test mode: periodic in x, no pressure ends */
+  int y_periodic; /* test mode: periodic in y, no walls */
+} orc_params;
+
+typedef struct {
+  orc_params p;
+  int N, Nx;
+  double mh[2];  /* masses normalised by m_min */
+  double s[2];   /* s_sigma = m_min / m_sigma */
+  double kT;     /* k_B T = c_s^2 m_min = 1/3 */
+  double mu, mu_s[2];
+  double rho_in[2], rho_out[2];
+  double C_in[2], C_out[2];
+  int light;
+  double Minv[Q][Q];
+  double *alpha;   /* [2][Nx] accommodation, bottom then top */
+  double *f;       /* pre-collision state  [2][9][N][Nx] */
+  double *fp;      /* post-collision state [2][9][N][Nx] */
+  int have_post;   /* fp holds collide(f) (or a state set by the caller) */
+  int post_only;   /* only fp is defined (state set by the caller, no step) */
+  long steps;
+} orc_sim;
+
+#define IDX(S, sp, i, j, x) ((((size_t)(sp) * Q + (i)) * (S)->N + (j)) * (S)->Nx + (x))
+
+/* ---------------------------------------------------------------------- */
+/* Special functions.                                                     */
+/* ---------------------------------------------------------------------- */
+
+/* Exponential integral E_i(x) = int_1^inf t^-1 e^{-xt} dt (the paper's E_i,
+ * below Eq. psi; it is E_1).  Power series (Abramowitz & Stegun 5.1.11) for
+ * x <= 1, continued fraction (A&S 5.1.22, evaluated with the modified Lentz
+ * method) for x > 1. */
+double orc_E1(double x) {
+  if (!(x >= 0.0)) return NAN; /* negative or NaN argument */
+  if (isinf(x)) return 0.0;
+  if (x == 0.0) return INFINITY;
+  if (x <= 1.0) {
+    double sum = 0.0, term = 1.0;
+    for (int k = 1; k < 200; ++k) {
+      term *= -x / k;            /* (-x)^k / k! */
+      double add = term / k;     /* (-x)^k / (k k!) */
+      sum += add;
+      if (fabs(add) < 1e-18 * fabs(sum)) break;
+    }
+    return -EULER_GAMMA - log(x) - sum;
+  }
+  /* E1(x) = e^{-x} / (x+1 - 1/(x+3 - 4/(x+5 - 9/(x+7 - ...)))) */
+  const double tiny = 1e-300;
+  double b = x + 1.0, c = 1.0 / tiny, d = 1.0 / b, h = d;
+  for (int k = 1; k < 10000; ++k) {
+    double a = -(double)k * k;
+    b += 2.0;
+    d = a * d + b;
+    if (fabs(d) < tiny) d = tiny;
+    c = b + a / c;
+    if (fabs(c) < tiny) c = tiny;
+    d = 1.0 / d;
+    double del = c * d;
+    h *= del;
+    if (fabs(del - 1.0) < 1e-17) break;
+  }
+  return h * exp(-x);
+}
+
+/* psi(alpha) = 1 + (alpha - 1) e^{-alpha} - alpha^2 E_i(alpha)  (Eq. psi). */
+double orc_psi(double a) {
+  if (a <= 0.0) return 0.0;
+  return 1.0 + (a - 1.0) * exp(-a) - a * a * orc_E1(a);
+}
+
+/* d psi / d alpha = 2 e^{-alpha} - 2 alpha E_i(alpha) (differentiating Eq.
+ * psi with dE_1/dx = -e^{-x}/x). */
+double orc_dpsi(double a) {
+  if (a <= 0.0) return 2.0;
+  return 2.0 * exp(-a) - 2.0 * a * orc_E1(a);
+}
+
+/* Wall-confinement factor Psi(y) = (psi(y/lambda) + psi((H-y)/lambda)) / 2
+ * (effective mean free path lambda_e = lambda Psi(y), Sec. 3.1). */
+double orc_Psi(double y, double H, double lam) {
+  return 0.5 * (orc_psi(y / lam) + orc_psi((H - y) / lam));
+}
+
+/* ---------------------------------------------------------------------- */
+/* Model pieces.                                                          */
+/* ---------------------------------------------------------------------- */
+
+/* Equilibrium of Eq. feq for one species. */
+static void feq(double rho_s, double s_s, double ux, double uy, double out[Q]) {
+  const double cs2 = 1.0 / 3.0;
+  const double usq = ux * ux + uy * uy;
+  for (int i = 0; i < Q; ++i) {
+    double alpha_i = (i == 0) ? (9.0 - 5.0 * s_s) / 4.0 : s_s;
+    double cu = CX[i] * ux + CY[i] * uy;
+    out[i] = WGT[i] * rho_s *
+             (alpha_i + cu / cs2 + cu * cu / (2.0 * cs2 * cs2) - usq / (2.0 * cs2));
+  }
+}
+
+void orc_feq(double rho_s, double s_s, double ux, double uy, double *out) {
+  feq(rho_s, s_s, ux, uy, out);
+}
+
+/* Gauss-Jordan inversion with partial pivoting (FP64). Returns 0 on success. */
+static int invert9(const double A[Q][Q], double R[Q][Q]) {
+  double a[Q][2 * Q];
+  for (int i = 0; i < Q; ++i)
+    for (int j = 0; j < 2 * Q; ++j)
+      a[i][j] = (j < Q) ? A[i][j] : (j - Q == i ? 1.0 : 0.0);
+  for (int col = 0; col < Q; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < Q; ++r)
+      if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+    if (a[piv][col] == 0.0) return -1;
+    if (piv != col)
+      for (int j = 0; j < 2 * Q; ++j) {
+        double t = a[col][j]; a[col][j] = a[piv][j]; a[piv][j] = t;
+      }
+    double d = a[col][col];
+    for (int j = 0; j < 2 * Q; ++j) a[col][j] /= d;
+    for (int r = 0; r < Q; ++r) {
+      if (r == col) continue;
+      double fct = a[r][col];
+      if (fct == 0.0) continue;
+      for (int j = 0; j < 2 * Q; ++j) a[r][j] -= fct * a[col][j];
+    }
+  }
+  for (int i = 0; i < Q; ++i)
+    for (int j = 0; j < Q; ++j) R[i][j] = a[i][Q + j];
+  return 0;
+}
+
+void orc_matrix_M(double *out) {
+  for (int i = 0; i < Q; ++i)
+    for (int j = 0; j < Q; ++j) out[i * Q + j] = MM[i][j];
+}
+
+void orc_matrix_Minv(double *out) {
+  double R[Q][Q];
+  invert9(MM, R);
+  for (int i = 0; i < Q; ++i)
+    for (int j = 0; j < Q; ++j) out[i * Q + j] = R[i][j];
+}
+
+/* One MRT collision of one species (Eqs. MRT, MR, S):
+ * f' = f - M^{-1} S (M f - M f^eq).  tau[k] is the relaxation time of moment
+ * k in the row order of M. */
+static void collide_species(const double Minv[Q][Q], const double f[Q],
+                            double rho_s, double s_s, double ux, double uy,
+                            const double tau[Q], double out[Q]) {
+  double fe[Q], m[Q], meq[Q], dm[Q];
+  feq(rho_s, s_s, ux, uy, fe);
+  for (int k = 0; k < Q; ++k) {
+    m[k] = 0.0;
+    meq[k] = 0.0;
+    for (int i = 0; i < Q; ++i) {
+      m[k] += MM[k][i] * f[i];
+      meq[k] += MM[k][i] * fe[i];
+    }
+    dm[k] = (m[k] - meq[k]) / tau[k];
+  }
+  for (int i = 0; i < Q; ++i) {
+    double acc = 0.0;
+    for (int k = 0; k < Q; ++k) acc += Minv[i][k] * dm[k];
+    out[i] = f[i] - acc;
+  }
+}
+
+/* Node-level moments and relaxation times (Sec. 3.1). */
+typedef struct {
+  double rho_s[2], j_s[2][2];
+  double rho, ux, uy;
+  double n_s[2], n, x_s[2], mx, p;
+  double lam, lam_s[2];
+  double tau_s, tau_d;
+} node_state;
+
+static void node_moments(const orc_sim *S, const double fa[Q], const double fb[Q],
+                         int j, node_state *ns) {
+  const double *fs[2] = {fa, fb};
+  ns->rho = 0.0;
+  double jx = 0.0, jy = 0.0;
+  for (int sp = 0; sp < 2; ++sp) {
+    double r = 0.0, ax = 0.0, ay = 0.0;
+    for (int i = 0; i < Q; ++i) {
+      r += fs[sp][i];
+      ax += CX[i] * fs[sp][i];
+      ay += CY[i] * fs[sp][i];
+    }
+    ns->rho_s[sp] = r;
+    ns->j_s[sp][0] = ax;
+    ns->j_s[sp][1] = ay;
+    ns->rho += r;
+    jx += ax;
+    jy += ay;
+  }
+  /* Eq. rhou: rho u = sum_s sum_i c_i f_si */
+  ns->ux = jx / ns->rho;
+  ns->uy = jy / ns->rho;
+  /* number densities, mole fractions, m_x = rho / n (below Eq. EQFrb) and
+   * p = n k_B T (Eq. P) */
+  ns->n = 0.0;
+  for (int sp = 0; sp < 2; ++sp) {
+    ns->n_s[sp] = ns->rho_s[sp] / S->mh[sp];
+    ns->n += ns->n_s[sp];
+  }
+  for (int sp = 0; sp < 2; ++sp) ns->x_s[sp] = ns->n_s[sp] / ns->n;
+  ns->mx = ns->rho / ns->n;
+  ns->p = ns->n * S->kT;
+  /* mean free paths from the viscosities (the lambda_sigma, lambda equation
+   * after Eq. EQFrsp), with the partial pressure for each species */
+  ns->lam = S->mu / ns->p * sqrt(PI * S->kT / (2.0 * ns->mx));
+  for (int sp = 0; sp < 2; ++sp) {
+    double p_s = ns->x_s[sp] * ns->p;
+    ns->lam_s[sp] = S->mu_s[sp] / p_s * sqrt(PI * S->kT / (2.0 * S->mh[sp]));
+  }
+  const double H = (double)S->N;
+  const double y = j + 0.5; /* wall at j = 1/2 of the 1-based row index */
+  /* Eq. taos (m_min = 1) */
+  ns->tau_s = 0.5 + ns->lam * orc_Psi(y, H, ns->lam) * sqrt(6.0 / (PI * ns->mx));
+  /* Eq. EQFrsp with effective species mean free paths */
+  double lae = ns->lam_s[0] * orc_Psi(y, H, ns->lam_s[0]);
+  double lbe = ns->lam_s[1] * orc_Psi(y, H, ns->lam_s[1]);
+  double m0 = S->mh[0] + S->mh[1];
+  double bracket = 1.0 / sqrt(ns->x_s[0] * lae) + 1.0 / sqrt(ns->x_s[1] * lbe);
+  ns->tau_d = 0.5 + 1.5 * sqrt(3.0 * m0 * S->mh[0] * S->mh[1] / (1.0 * ns->mx * ns->mx)) /
+                        (bracket * bracket);
+}
+
+/* tau_q of Eq. taoq from a wall node's mixture mean free path, m_x and
+ * accommodation coefficient alpha (Eq. A12); dx = 1, H = N. */
+double orc_tau_q(double lam_w, double mx_w, double alpha, double H) {
+  const double vs = sqrt(PI / 6.0); /* varsigma */
+  const double g = sqrt(6.0 / (PI * mx_w));
+  /* tilde tau_s(0) = tau_s(0) - 1/2 with Psi(0) = psi(H/lambda)/2 */
+  double tt = lam_w * orc_Psi(0.0, H, lam_w) * g;
+  /* tau'_s(0) = d tilde tau_s / dy at y = 0
+   *           = (g/2) [psi'(0) - psi'(H/lambda)] */
+  double dtt = 0.5 * g * (orc_dpsi(0.0) - orc_dpsi(H / lam_w));
+  double A1 = (2.0 - alpha) / alpha * (1.0 - 0.1817 * alpha);
+  double A2 = 1.0 / PI + 0.5 * A1 * A1;
+  double dx = 1.0;
+  return 0.5 + (3.0 + 24.0 * vs * vs * tt * tt * A2) / (16.0 * tt) +
+         dtt * dx * (12.0 + 30.0 * tt * vs * A1) / (16.0 * tt * tt);
+}
+
+/* tilde tau_s(y) = lambda Psi(y) sqrt(6/(pi m_x)) for frozen lambda, m_x. */
+double orc_tau_s_tilde(double y, double H, double lam, double mx) {
+  return lam * orc_Psi(y, H, lam) * sqrt(6.0 / (PI * mx));
+}
+
+/* r_sigma of Eq. R (first printed form) with c_m = c_m0 (2 - alpha)/alpha. */
+static double dbb_r(const orc_sim *S, double mx_w, double alpha) {
+  double cm = S->p.c_m0 * (2.0 - alpha) / alpha;
+  return 2.0 - 2.0 / (1.0 + cm / 3.0 * sqrt(PI * mx_w / (2.0 * S->kT)));
+}
+
+double orc_dbb_r(double c_m0, double alpha, double mx_w) {
+  double cm = c_m0 * (2.0 - alpha) / alpha;
+  return 2.0 - 2.0 / (1.0 + cm / 3.0 * sqrt(PI * mx_w / (2.0 * (1.0 / 3.0))));
+}
+
+/* ---------------------------------------------------------------------- */
+/* Simulation.                                                            */
+/* ---------------------------------------------------------------------- */
+
+static void get_node(const orc_sim *S, const double *arr, int x, int j,
+                     double fa[Q], double fb[Q]) {
+  for (int i = 0; i < Q; ++i) {
+    fa[i] = arr[IDX(S, 0, i, j, x)];
+    fb[i] = arr[IDX(S, 1, i, j, x)];
+  }
+}
+
+static int is_interior_col(const orc_sim *S, int x) {
+  return S->p.x_periodic ? 1 : (x >= 1 && x <= S->Nx - 2);
+}
+
+orc_sim *orc_create(const orc_params *p) {
+  if (!p) return NULL;
+  if (!(p->m_a > 0 && p->m_b > 0 && p->C_l > 0 && p->C_l < 1 && p->theta >= 1 &&
+        p->Kn_out > 0 && p->N >= 2 && p->N_x >= 4 && p->accommodation > 0 &&
+        p->accommodation <= 1 && p->tau_rho > 0.5 && p->tau_e > 0.5 &&
+        p->tau_eps > 0.5 && p->mu_ratio_a > 0 && p->mu_ratio_b > 0))
+    return NULL;
+  orc_sim *S = (orc_sim *)calloc(1, sizeof(orc_sim));
+  S->p = *p;
+  S->N = p->N;
+  S->Nx = p->N_x;
+  double m_min = fmin(p->m_a, p->m_b);
+  S->mh[0] = p->m_a / m_min;
+  S->mh[1] = p->m_b / m_min;
+  S->s[0] = m_min / p->m_a;
+  S->s[1] = m_min / p->m_b;
+  S->kT = (1.0 / 3.0) * 1.0; /* c_s^2 m_min with m_min = 1 */
+  S->light = (p->m_a <= p->m_b) ? 0 : 1;
+  double clo = (p->C_l_out < 0) ? p->C_l : p->C_l_out;
+  S->C_in[S->light] = p->C_l;
+  S->C_in[1 - S->light] = 1.0 - p->C_l;
+  S->C_out[S->light] = clo;
+  S->C_out[1 - S->light] = 1.0 - clo;
+  const double n_out = 1.0, n_in = p->theta * n_out;
+  /* mu from lambda_out = Kn_out H at the outlet state */
+  double mx_out = S->C_out[0] * S->mh[0] + S->C_out[1] * S->mh[1];
+  double p_out = n_out * S->kT;
+  double lam_out = p->Kn_out * (double)p->N;
+  S->mu = lam_out * p_out / sqrt(PI * S->kT / (2.0 * mx_out));
+  S->mu_s[0] = p->mu_ratio_a * S->mu;
+  S->mu_s[1] = p->mu_ratio_b * S->mu;
+  for (int sp = 0; sp < 2; ++sp) {
+    /* rho_s = p_s / (s_s c_s^2) with p_s = C_s n k_B T */
+    S->rho_in[sp] = (S->C_in[sp] * n_in * S->kT) / (S->s[sp] * (1.0 / 3.0));
+    S->rho_out[sp] = (S->C_out[sp] * n_out * S->kT) / (S->s[sp] * (1.0 / 3.0));
+  }
+  if (invert9(MM, S->Minv) != 0) { free(S); return NULL; }
+  size_t nn = (size_t)2 * Q * S->N * S->Nx;
+  S->f = (double *)calloc(nn, sizeof(double));
+  S->fp = (double *)calloc(nn, sizeof(double));
+  S->alpha = (double *)malloc(sizeof(double) * 2 * S->Nx);
+  if (!S->f || !S->fp || !S->alpha) {
+    free(S->f); free(S->fp); free(S->alpha); free(S);
+    return NULL;
+  }
+  for (int k = 0; k < 2 * S->Nx; ++k) S->alpha[k] = p->accommodation;
+  return S;
+}
+
+void orc_destroy(orc_sim *S) {
+  if (!S) return;
+  free(S->f); free(S->fp); free(S->alpha);
+  free(S);
+}
+
+int orc_set_accommodation_field(orc_sim *S, const double *alpha, long n) {
+  if (!S || !alpha || n != 2L * S->Nx) return -1;
+  for (long k = 0; k < n; ++k)
+    if (!(alpha[k] > 0 && alpha[k] <= 1)) return -1;
+  memcpy(S->alpha, alpha, sizeof(double) * n);
+  return 0;
+}
+
+/* Initial state: pressure linear from theta p_out at column 0 to p_out at
+ * column N_x - 1, zero velocity, mole fraction linear between the end values
+ * (uniform when they are equal), f = f^eq (the paper gives no initial
+ * condition). Periodic-x mode uses the outlet state everywhere. */
+void orc_init(orc_sim *S) {
+  double fe[Q];
+  for (int x = 0; x < S->Nx; ++x) {
+    double t = S->p.x_periodic ? 1.0 : (double)x / (S->Nx - 1);
+    double n = S->p.theta + (1.0 - S->p.theta) * t;
+    if (S->p.x_periodic) n = 1.0;
+    for (int sp = 0; sp < 2; ++sp) {
+      double C = S->C_in[sp] + (S->C_out[sp] - S->C_in[sp]) * t;
+      double rho_s = n * C * S->mh[sp];
+      feq(rho_s, S->s[sp], 0.0, 0.0, fe);
+      for (int j = 0; j < S->N; ++j)
+        for (int i = 0; i < Q; ++i) S->f[IDX(S, sp, i, j, x)] = fe[i];
+    }
+  }
+  S->have_post = 0;
+  S->post_only = 0;
+  S->steps = 0;
+}
+
+/* Caller-provided post-collision state, canonical layout [2][9][N][N_x]. */
+int orc_set_post_state(orc_sim *S, const double *fp) {
+  if (!S || !fp) return -1;
+  memcpy(S->fp, fp, sizeof(double) * 2 * Q * S->N * S->Nx);
+  S->have_post = 1;
+  S->post_only = 1;
+  S->steps = 0;
+  return 0;
+}
+
+/* Step 1 + 2 over the whole lattice: f -> fp. */
+static void collide_all(orc_sim *S) {
+  const int N = S->N, Nx = S->Nx;
+  const double H = (double)N;
+  double *tq_bot = (double *)malloc(sizeof(double) * Nx);
+  double *tq_top = (double *)malloc(sizeof(double) * Nx);
+  /* tau_q per column from the two wall nodes (rows 1 and N). */
+  for (int x = 0; x < Nx; ++x) {
+    if (!is_interior_col(S, x)) { tq_bot[x] = tq_top[x] = 1.0; continue; }
+    double fa[Q], fb[Q];
+    node_state ns;
+    get_node(S, S->f, x, 0, fa, fb);
+    node_moments(S, fa, fb, 0, &ns);
+    tq_bot[x] = orc_tau_q(ns.lam, ns.mx, S->alpha[x], H);
+    get_node(S, S->f, x, N - 1, fa, fb);
+    node_moments(S, fa, fb, N - 1, &ns);
+    tq_top[x] = orc_tau_q(ns.lam, ns.mx, S->alpha[Nx + x], H);
+  }
+#pragma omp parallel for schedule(static)
+  for (int x = 0; x < Nx; ++x) {
+    if (!is_interior_col(S, x)) continue;
+    for (int j = 0; j < N; ++j) {
+      double fa[Q], fb[Q], out[Q];
+      node_state ns;
+      get_node(S, S->f, x, j, fa, fb);
+      node_moments(S, fa, fb, j, &ns);
+      /* row nearer to the bottom wall (1-based J with 2J <= N + 1) */
+      double tq = (2 * (j + 1) <= N + 1) ? tq_bot[x] : tq_top[x];
+      double tau[Q] = {S->p.tau_rho, S->p.tau_e, S->p.tau_eps, ns.tau_d, tq,
+                       ns.tau_d,     tq,         ns.tau_s,     ns.tau_s};
+      const double *fs[2] = {fa, fb};
+      for (int sp = 0; sp < 2; ++sp) {
+        collide_species(S->Minv, fs[sp], ns.rho_s[sp], S->s[sp], ns.ux, ns.uy, tau, out);
+        for (int i = 0; i < Q; ++i) S->fp[IDX(S, sp, i, j, x)] = out[i];
+      }
+    }
+  }
+  free(tq_bot);
+  free(tq_top);
+}
+
+static double col_density(const orc_sim *S, const double *arr, int sp, int x, int j) {
+  double r = 0.0;
+  for (int i = 0; i < Q; ++i) r += arr[IDX(S, sp, i, j, x)];
+  return r;
+}
+
+/* Density-correction factor of Eq. rho2 for the ghost column extrapolated
+ * from columns x1 (first layer) and x2 (second layer) of arr. */
+static double ghost_kappa(const orc_sim *S, const double *arr, int sp, int x1, int x2,
+                          double rho_target) {
+  double sum = 0.0;
+  for (int j = 0; j < S->N; ++j)
+    sum += 2.0 * col_density(S, arr, sp, x1, j) - col_density(S, arr, sp, x2, j);
+  return S->N * rho_target / sum;
+}
+
+/* Steps 3-5: ghost columns, push streaming, diffuse bounce-back. */
+static void stream_and_bound(orc_sim *S) {
+  const int N = S->N, Nx = S->Nx;
+  const double *P = S->fp;
+  double *F = S->f;
+  /* Ghost columns (Eqs. rho1, rho2) from the post-collision state. */
+  double kin[2] = {1, 1}, kout[2] = {1, 1};
+  if (!S->p.x_periodic) {
+    for (int sp = 0; sp < 2; ++sp) {
+      kin[sp] = ghost_kappa(S, P, sp, 1, 2, S->rho_in[sp]);
+      kout[sp] = ghost_kappa(S, P, sp, Nx - 2, Nx - 3, S->rho_out[sp]);
+    }
+  }
+  /* Push: every source node (including the ghost columns) sends f'_i to
+   * x + c_i; destinations outside the interior are dropped. */
+  for (int sp = 0; sp < 2; ++sp)
+    for (int i = 0; i < Q; ++i)
+      for (int j = 0; j < N; ++j)
+        for (int x = 0; x < Nx; ++x) {
+          double val;
+          if (!S->p.x_periodic && x == 0)
+            val = kin[sp] * (2.0 * P[IDX(S, sp, i, j, 1)] - P[IDX(S, sp, i, j, 2)]);
+          else if (!S->p.x_periodic && x == Nx - 1)
+            val = kout[sp] * (2.0 * P[IDX(S, sp, i, j, Nx - 2)] - P[IDX(S, sp, i, j, Nx - 3)]);
+          else
+            val = P[IDX(S, sp, i, j, x)];
+          int xd = x + CX[i], jd = j + CY[i];
+          if (S->p.x_periodic) xd = (xd + Nx) % Nx;
+          if (S->p.y_periodic) jd = (jd + N) % N;
+          if (jd < 0 || jd >= N) continue;     /* leaves through a wall */
+          if (!is_interior_col(S, xd)) continue; /* into a ghost column */
+          F[IDX(S, sp, i, jd, xd)] = val;
+        }
+  if (S->p.y_periodic) return;
+  /* Diffuse bounce-back (Eqs. bot, bot2) at rows 1 and N, from the
+   * post-collision populations of the same node. */
+  static const int BOT_UNK[3] = {2, 5, 6}, TOP_UNK[3] = {4, 7, 8};
+  static const int OPPQ[Q] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+  for (int wall = 0; wall < 2; ++wall) {
+    int j = wall == 0 ? 0 : N - 1;
+    const int *unk = wall == 0 ? BOT_UNK : TOP_UNK;
+    for (int x = 0; x < Nx; ++x) {
+      if (!is_interior_col(S, x)) continue;
+      /* r_sigma from the mixture mass of the reflected (post-collision)
+       * state at this wall node */
+      double rho = 0.0, n = 0.0;
+      for (int sp = 0; sp < 2; ++sp) {
+        double r = col_density(S, P, sp, x, j);
+        rho += r;
+        n += r / S->mh[sp];
+      }
+      double alpha = S->alpha[wall * Nx + x];
+      double r_w = dbb_r(S, rho / n, alpha);
+      for (int sp = 0; sp < 2; ++sp) {
+        /* wall density with zero normal flux of this species:
+         * sum_unknown f^eq_i(rho_w, u_w) = sum_outgoing f'_i */
+        double out_sum = 0.0, eq_unit[Q], wsum = 0.0;
+        for (int k = 0; k < 3; ++k) out_sum += P[IDX(S, sp, OPPQ[unk[k]], j, x)];
+        feq(1.0, S->s[sp], 0.0, 0.0, eq_unit);
+        for (int k = 0; k < 3; ++k) wsum += eq_unit[unk[k]];
+        double rho_w = out_sum / wsum;
+        double fw[Q];
+        feq(rho_w, S->s[sp], 0.0, 0.0, fw); /* u_w = 0 */
+        for (int k = 0; k < 3; ++k) {
+          int i = unk[k];
+          F[IDX(S, sp, i, j, x)] = r_w * fw[i] + (1.0 - r_w) * P[IDX(S, sp, OPPQ[i], j, x)];
+        }
+      }
+    }
+  }
+}
+
+void orc_step(orc_sim *S, long nsteps) {
+  for (long t = 0; t < nsteps; ++t) {
+    if (!S->have_post) collide_all(S);
+    stream_and_bound(S);
+    S->have_post = 0;
+    S->post_only = 0;
+    S->steps++;
+  }
+}
+
+/* Post-collision state of the current step, canonical layout. */
+void orc_get_post_state(orc_sim *S, double *out) {
+  if (!S->have_post) {
+    collide_all(S);
+    S->have_post = 1;
+  }
+  memcpy(out, S->fp, sizeof(double) * 2 * Q * S->N * S->Nx);
+}
+
+/* Pre-collision state, canonical layout (undefined before the first step
+ * when the state was set as post-collision; the post state is returned). */
+void orc_get_state(orc_sim *S, double *out) {
+  memcpy(out, S->post_only ? S->fp : S->f, sizeof(double) * 2 * Q * S->N * S->Nx);
+}
+
+long orc_steps(const orc_sim *S) { return S->steps; }
+int orc_Nx(const orc_sim *S) { return S->Nx; }
+
+/* Macroscopic fields of the current state (Eq. rhou): rho_s and the species
+ * velocity u_s from rho_s u_s = (2 tau_d - 1)/(2 tau_d) sum_i c_i f_si +
+ * rho_s u / (2 tau_d).  Arrays are [N][N_x]; any may be NULL.  In pressure
+ * mode columns 0 and N_x - 1 hold the boundary-node values of Eqs. rho1 and
+ * rho2 applied to the fields: rho_s = kappa_s (2 rho_s(1) - rho_s(2)) and
+ * u_s = 2 u_s(1) - u_s(2). */
+void orc_moments(orc_sim *S, double *rho_a, double *rho_b, double *ua_x, double *ua_y,
+                 double *ub_x, double *ub_y) {
+  const int N = S->N, Nx = S->Nx;
+  const double *arr = S->post_only ? S->fp : S->f;
+  double *outs[6] = {rho_a, rho_b, ua_x, ua_y, ub_x, ub_y};
+  size_t nn = (size_t)N * Nx;
+  double *buf = (double *)calloc(6 * nn, sizeof(double));
+  for (int x = 0; x < Nx; ++x) {
+    if (!is_interior_col(S, x)) continue;
+    for (int j = 0; j < N; ++j) {
+      double fa[Q], fb[Q];
+      node_state ns;
+      get_node(S, arr, x, j, fa, fb);
+      node_moments(S, fa, fb, j, &ns);
+      for (int sp = 0; sp < 2; ++sp) {
+        double w1 = (2.0 * ns.tau_d - 1.0) / (2.0 * ns.tau_d);
+        double w2 = 1.0 / (2.0 * ns.tau_d);
+        double mx = w1 * ns.j_s[sp][0] + w2 * ns.rho_s[sp] * ns.ux;
+        double my = w1 * ns.j_s[sp][1] + w2 * ns.rho_s[sp] * ns.uy;
+        buf[sp * nn + (size_t)j * Nx + x] = ns.rho_s[sp];
+        buf[(2 + 2 * sp) * nn + (size_t)j * Nx + x] = mx / ns.rho_s[sp];
+        buf[(3 + 2 * sp) * nn + (size_t)j * Nx + x] = my / ns.rho_s[sp];
+      }
+    }
+  }
+  if (!S->p.x_periodic) {
+    for (int end = 0; end < 2; ++end) {
+      int xb = end == 0 ? 0 : Nx - 1, x1 = end == 0 ? 1 : Nx - 2, x2 = end == 0 ? 2 : Nx - 3;
+      for (int sp = 0; sp < 2; ++sp) {
+        double target = end == 0 ? S->rho_in[sp] : S->rho_out[sp];
+        double sum = 0.0;
+        for (int j = 0; j < N; ++j)
+          sum += 2.0 * buf[sp * nn + (size_t)j * Nx + x1] - buf[sp * nn + (size_t)j * Nx + x2];
+        double kap = N * target / sum;
+        for (int j = 0; j < N; ++j) {
+          size_t o = (size_t)j * Nx;
+          buf[sp * nn + o + xb] =
+              kap * (2.0 * buf[sp * nn + o + x1] - buf[sp * nn + o + x2]);
+          for (int c = 0; c < 2; ++c) {
+            size_t f = (size_t)(2 + 2 * sp + c) * nn;
+            buf[f + o + xb] = 2.0 * buf[f + o + x1] - buf[f + o + x2];
+          }
+        }
+      }
+    }
+  }
+  for (int k = 0; k < 6; ++k)
+    if (outs[k]) memcpy(outs[k], buf + k * nn, sizeof(double) * nn);
+  free(buf);
+}
+
+/* Separation diagnostics of the current state (Eqs. C, CL, Clline):
+ * C_l(x) = sum_j n_l / sum_j (n_a + n_b) over the column; CL from the minimum
+ * over the updated columns and the imposed C_l,in; C~_l over all N_x columns
+ * with the boundary columns at their imposed values; mdot_s = mean over the
+ * updated columns of sum_j rho_s u_s,x.  Cl_profile (N_x) may be NULL. */
+void orc_separation(orc_sim *S, double *CL, double *Cl_tilde, double *mdot_a,
+                    double *mdot_b, double *Cl_profile, int *x_min) {
+  const int N = S->N, Nx = S->Nx;
+  size_t nn = (size_t)N * Nx;
+  double *m = (double *)malloc(sizeof(double) * 6 * nn);
+  orc_moments(S, m, m + nn, m + 2 * nn, m + 3 * nn, m + 4 * nn, m + 5 * nn);
+  double *prof = (double *)malloc(sizeof(double) * Nx);
+  double Cin = S->C_in[S->light], Cout = S->C_out[S->light];
+  double cmin = INFINITY, tsum = 0.0, md[2] = {0, 0};
+  int xm = -1, ncol = 0;
+  for (int x = 0; x < Nx; ++x) {
+    if (!is_interior_col(S, x)) {
+      prof[x] = (x == 0) ? Cin : Cout;
+      tsum += prof[x] - Cin;
+      continue;
+    }
+    double ns[2] = {0, 0};
+    for (int j = 0; j < N; ++j)
+      for (int sp = 0; sp < 2; ++sp) {
+        double r = m[sp * nn + (size_t)j * Nx + x];
+        ns[sp] += r / S->mh[sp];
+        md[sp] += r * m[(2 + 2 * sp) * nn + (size_t)j * Nx + x];
+      }
+    prof[x] = ns[S->light] / (ns[0] + ns[1]);
+    tsum += prof[x] - Cin;
+    if (prof[x] < cmin) { cmin = prof[x]; xm = x; }
+    ncol++;
+  }
+  if (CL) *CL = (Cin - cmin) / Cin;
+  if (Cl_tilde) *Cl_tilde = tsum / (Nx * Cin);
+  if (mdot_a) *mdot_a = md[0] / ncol;
+  if (mdot_b) *mdot_b = md[1] / ncol;
+  if (x_min) *x_min = xm;
+  if (Cl_profile) memcpy(Cl_profile, prof, sizeof(double) * Nx);
+  free(prof);
+  free(m);
+}
+
+/* Species mass crossing each face x + 1/2 (x = 0..N_x-2) during the next
+ * streaming: sum_j [sum_{c_x>0} f'(x,j) - sum_{c_x<0} f'(x+1,j)], from the
+ * post-collision state (ghost columns included). */
+void orc_face_flux(orc_sim *S, double *Fa, double *Fb) {
+  const int N = S->N, Nx = S->Nx;
+  if (!S->have_post) { collide_all(S); S->have_post = 1; }
+  const double *P = S->fp;
+  double kin[2] = {1, 1}, kout[2] = {1, 1};
+  if (!S->p.x_periodic)
+    for (int sp = 0; sp < 2; ++sp) {
+      kin[sp] = ghost_kappa(S, P, sp, 1, 2, S->rho_in[sp]);
+      kout[sp] = ghost_kappa(S, P, sp, Nx - 2, Nx - 3, S->rho_out[sp]);
+    }
+  double *outs[2] = {Fa, Fb};
+  for (int sp = 0; sp < 2; ++sp)
+    for (int x = 0; x + 1 < Nx; ++x) {
+      double acc = 0.0;
+      for (int j = 0; j < N; ++j)
+        for (int i = 0; i < Q; ++i) {
+          int src = CX[i] > 0 ? x : (CX[i] < 0 ? x + 1 : -1);
+          if (src < 0) continue;
+          int jd = j + CY[i];
+          if (!S->p.y_periodic && (jd < 0 || jd >= N)) continue;
+          double v;
+          if (!S->p.x_periodic && src == 0)
+            v = kin[sp] * (2.0 * P[IDX(S, sp, i, j, 1)] - P[IDX(S, sp, i, j, 2)]);
+          else if (!S->p.x_periodic && src == Nx - 1)
+            v = kout[sp] * (2.0 * P[IDX(S, sp, i, j, Nx - 2)] - P[IDX(S, sp, i, j, Nx - 3)]);
+          else
+            v = P[IDX(S, sp, i, j, src)];
+          acc += CX[i] * v;
+        }
+      outs[sp][x] = acc;
+    }
+}
+
+/* Node-level entry points used by the pin tests. */
+void orc_node_taus(orc_sim *S, const double *fa, const double *fb, int j, double *out) {
+  node_state ns;
+  node_moments(S, fa, fb, j, &ns);
+  out[0] = ns.tau_s;
+  out[1] = ns.tau_d;
+  out[2] = ns.lam;
+  out[3] = ns.lam_s[0];
+  out[4] = ns.lam_s[1];
+  out[5] = ns.mx;
+  out[6] = ns.ux;
+  out[7] = ns.uy;
+}
+
+/* One collision of one node with caller-given relaxation times tau[9]
+ * (row order of M); rho_s and u from the node itself. */
+void orc_collide_node(orc_sim *S, const double *fa, const double *fb, const double *tau,
+                      double *outa, double *outb) {
+  node_state ns;
+  node_moments(S, fa, fb, 0, &ns);
+  collide_species(S->Minv, fa, ns.rho_s[0], S->s[0], ns.ux, ns.uy, tau, outa);
+  collide_species(S->Minv, fb, ns.rho_s[1], S->s[1], ns.ux, ns.uy, tau, outb);
+}
+
+/* Lattice constants derived at creation: mu, mu_a, mu_b, rho_in[2],
+ * rho_out[2], s[2], mh[2]. */
+void orc_constants(const orc_sim *S, double *out) {
+  out[0] = S->mu;
+  out[1] = S->mu_s[0];
+  out[2] = S->mu_s[1];
+  out[3] = S->rho_in[0];
+  out[4] = S->rho_in[1];
+  out[5] = S->rho_out[0];
+  out[6] = S->rho_out[1];
+  out[7] = S->s[0];
+  out[8] = S->s[1];
+  out[9] = S->mh[0];
+  out[10] = S->mh[1];
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

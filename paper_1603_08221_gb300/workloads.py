@@ -1,0 +1,71 @@
+"""Seeded synthetic workloads for the two-species microchannel problem.
+
+This module holds problem definitions and random-number draws only: gas
+pairs, the channel shapes of the paper's parametric study (Table 1 and the
+20 x 700 lattice of Sec. 2) scaled to the benchmark sizes, random
+post-collision states for the invariant tests and random wall accommodation
+fields.  It contains none of the method's arithmetic, so both the CUDA path
+and the FP64 oracle can take their inputs from it.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# Molecular masses (g/mol) of the paper's two mixtures (Sec. 2).
+HE, NE, AR = 4.003, 20.18, 39.948
+
+#: Named problems. Each is a dict of the physical inputs of Sec. 2 (masses,
+#: light-species mole fraction, pressure ratio, outlet Knudsen number, cells
+#: across the channel and aspect ratio).
+PRESETS = {
+    # He-Ar, 320 x 16 channel, 20 000 steps: GPU against the oracle.
+    "heli_argon_320x16": dict(m_a=HE, m_b=AR, C_l=0.5, theta=2.0, Kn_out=0.1,
+                              N=16, L_over_H=20.0),
+    # Ne-Ar, 32768 x 512 channel: the throughput workload.
+    "neon_argon_32768x512": dict(m_a=NE, m_b=AR, C_l=0.3, theta=3.0, Kn_out=0.05,
+                                 N=512, L_over_H=64.0),
+    # Its 1/16 linear-scale copy (2048 x 32), same C_l, theta, Kn_out.
+    "neon_argon_2048x32": dict(m_a=NE, m_b=AR, C_l=0.3, theta=3.0, Kn_out=0.05,
+                               N=32, L_over_H=64.0),
+    # He-Ar 1280 x 64 (sensitivity workload shape).
+    "heli_argon_1280x64": dict(m_a=HE, m_b=AR, C_l=0.5, theta=2.0, Kn_out=0.2,
+                               N=64, L_over_H=20.0),
+    # Ne-Ar 16384 x 256 (reduced-precision storage workload shape).
+    "neon_argon_16384x256": dict(m_a=NE, m_b=AR, C_l=0.5, theta=2.5, Kn_out=0.5,
+                                 N=256, L_over_H=64.0),
+    # The paper's own lattice (20 x 700), Case 2 at Kn_out = 0.3, theta = 2.
+    "paper_case2_700x20": dict(m_a=HE, m_b=AR, C_l=0.5, theta=2.0, Kn_out=0.3,
+                               N=20, L_over_H=35.0),
+}
+
+
+def preset(name: str, **override) -> dict:
+    p = dict(PRESETS[name])
+    p.update(override)
+    return p
+
+
+def n_x(params: dict) -> int:
+    """Number of lattice columns, N_x = round(N * L/H)."""
+    if "N_x" in params:
+        return int(params["N_x"])
+    return int(round(params["N"] * params["L_over_H"]))
+
+
+def random_post_state(N: int, N_x: int, seed: int, lo: float = 0.05,
+                      hi: float = 0.15, dtype=np.float64) -> np.ndarray:
+    """Non-negative random populations, layout [species][i][row][column].
+
+    Species b gets ten times the mass of species a so that both carry
+    comparable number densities for a 1:10 mass ratio."""
+    rng = np.random.default_rng(seed)
+    f = rng.uniform(lo, hi, size=(2, 9, N, N_x))
+    f[1] *= 10.0
+    return f.astype(dtype)
+
+
+def random_accommodation(N_x: int, seed: int, spread: float = 0.05) -> np.ndarray:
+    """Per-wall-node accommodation field, bottom wall then top wall, drawn as
+    1 - U(0, spread) so that it stays in (0, 1]."""
+    rng = np.random.default_rng(seed)
+    return 1.0 - rng.uniform(0.0, spread, size=2 * N_x)
