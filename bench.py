@@ -1,0 +1,301 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the fused two-species MRT-LBM step on GB300.
+
+One benchmark step is one lattice Boltzmann time step of the whole hot path
+(pull-stream + DBB walls + pressure ends + moments + effective relaxation
+times + MRT collision + FP64 column reductions and separation diagnostics),
+i.e. one launch of the fused kernel over the Ne-Ar 32768 x 512 channel
+(16.8 M nodes, two species, 2.4 GB of FP32 populations: larger than L2, so no
+flush is needed between steps).
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 oracle on
+the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_NODE = 2 * 9 * 4 * 2  # two species x 9 populations x FP32 x (read + write)
+WORKLOAD = "neon_argon_32768x512"
+REF_SAMPLE = "neon_argon_2048x32"  # 1/16 linear-scale copy (same C_l, theta, Kn_out)
+KERNEL = "lbm_step_kernel"
+PROFILE_MD = os.path.join(ROOT, "profiles", "lbm_step_kernel_neon_argon_32768x512.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_1603_08221_gb300", "csrc", "lbm_mix.cu")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate(elapsed_per_rank, units_per_rank):
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    t = max(elapsed_per_rank)
+    return sum(units_per_rank) / t, t
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(
+                    ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                     "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                for line in out.stdout.strip().splitlines():
+                    self.rows.append([c.strip() for c in line.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    try:
+        text = open(PROFILE_MD).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    if not m or not h:
+        return None
+    cur = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    return float(m.group(1)) if h.group(1) == cur else None
+
+
+def oracle_throughput(steps: int, sample: str):
+    """FP64 oracle MLUPS on the host cores over `steps` steps of `sample`."""
+    import oracle
+    from paper_1603_08221_gb300 import workloads
+
+    p = workloads.preset(sample)
+    o = oracle.Oracle(p)
+    o.init()
+    o.step(1)  # untimed first step (page-in)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    nodes = o.N * (o.N_x - 2)
+    return nodes * steps / dt / 1e6, dt, oracle.num_threads(), nodes
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    from paper_1603_08221_gb300 import workloads
+    p = workloads.preset(REF_SAMPLE)
+    o = oracle.Oracle(p)
+    o.init()
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    nodes = o.N * (o.N_x - 2)
+    mlups = nodes * args.steps / dt / 1e6
+    sample = (f"FP64 oracle, {o.N_x}x{o.N} 1/16 linear-scale copy of the {WORKLOAD} "
+              f"workload (same gases, C_l, theta, Kn_out), {args.steps} steps")
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": REF_SAMPLE},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1603_08221_gb300 import binding, workloads
+    binding.load()
+    p = workloads.preset(args.workload)
+    stream = torch.cuda.current_stream(dev)
+    sim = binding.LbmMix(stream=stream, **p)
+    nodes = sim.N * (sim.N_x - 2)
+    sim.init()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---------------- device-resident timing: K fused launches, inputs in HBM
+    binding.lbm_mix_step(sim.h, args.warmup)
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        binding.lbm_mix_step(sim.h, args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+    barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    sep = sim.separation()  # raises on a non-finite state
+
+    # ---------------- end to end through the C ABI with host buffers
+    f_host = torch.empty((2, 9, sim.N, sim.N_x), dtype=torch.float32, pin_memory=True)
+    f_np = f_host.numpy()
+    f_np[...] = sim.get_post_state()
+    outs = [torch.empty((sim.N, sim.N_x), dtype=torch.float64, pin_memory=True)
+            for _ in range(6)]
+    ptrs = [o.numpy() for o in outs]
+    lib = binding.load()
+    import ctypes
+    barrier()
+    t0 = time.perf_counter()
+    binding.lbm_mix_set_post_state(sim.h, f_np)
+    binding.lbm_mix_step(sim.h, args.steps)
+    st = lib.lbm_mix_moments(sim.h, *[binding._dptr(a) for a in ptrs])
+    assert st == 0, binding.lbm_mix_last_error()
+    sep_e2e = sim.separation()
+    barrier()
+    e2e_elapsed = time.perf_counter() - t0
+    h2d = f_np.nbytes
+    d2h = sum(a.nbytes for a in ptrs) + 8 * (sim.N_x + 8)
+
+    # ---------------- whole-job aggregation (max time over ranks)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed, e2e_elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed, e2e_elapsed = float(t[0]), float(t[1])
+    mlups, _ = aggregate([elapsed] * 1, [nodes * args.steps * world])
+    mlups /= 1e6
+    e2e_mlups = nodes * args.steps * world / e2e_elapsed / 1e6
+    ms_per_step = elapsed / args.steps * 1e3
+
+    if rank != 0:
+        return 0
+    peak, peak_kind = measured_peak_hbm()
+    achieved = BYTES_PER_NODE * nodes / (elapsed / args.steps) / 1e9
+    traffic = profiled_traffic()
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        c_mlups, c_dt, cores, c_nodes = oracle_throughput(args.cpu_steps, REF_SAMPLE)
+        cpu = {"value": c_mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"FP64 oracle, {args.cpu_steps} steps of the {REF_SAMPLE} 1/16 "
+                         f"linear-scale copy ({c_nodes} nodes, {c_dt:.1f} s)"}
+    line = {
+        "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "N": sim.N, "N_x": sim.N_x,
+                   "m_a": p["m_a"], "m_b": p["m_b"], "C_l": p["C_l"], "theta": p["theta"],
+                   "Kn_out": p["Kn_out"], "nodes_updated": nodes,
+                   "bytes_per_node_step": BYTES_PER_NODE,
+                   "l2": "state (2 x 1.2 GB FP32) larger than L2; no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": peak_kind, "kernel": KERNEL},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
+                "d2h_bytes_per_step": d2h / args.steps},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "result": {"CL": sep["CL"], "Cl_tilde": sep["Cl_tilde"], "mdot_a": sep["mdot_a"],
+                   "mdot_b": sep["mdot_b"], "CL_e2e_run": sep_e2e["CL"]},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,169 @@
+/*
+ * lbm_mix.h — C ABI of the GB300 (sm_103a) two-species lattice Boltzmann hot
+ * path for a rarefied binary gas mixture in a pressure-driven microchannel.
+ *
+ * Method: Wang, Xu & Guo, "Lattice Boltzmann simulation of separation
+ * phenomenon in a binary gaseous flow through a microchannel"
+ * (arXiv:1603.08221), Sec. 3: D2Q9 multiple-relaxation-time LBE for each
+ * species (Eqs. MRT, MR, m, S, feq, rhou), Knudsen-dependent effective
+ * relaxation times (Eqs. EQFrb, EQFrsp, psi, taos), diffuse-bounce-back walls
+ * (Eqs. bot, bot2, R, taoq, A12) and extrapolation-correction pressure ends
+ * (Eqs. rho1, rho2); separation diagnostics of Sec. 2 (Eqs. C, CL, Clline).
+ *
+ * Conventions for every call:
+ *  - Lattice units: dx = dt = 1, c_s^2 = k_B T / m_min = 1/3, masses
+ *    normalised by m_min, outlet number density 1, channel height H = N.
+ *  - The lattice has N rows (j = 0 .. N-1; the bottom wall sits half a cell
+ *    below row 0, the top wall half a cell above row N-1) and N_x columns
+ *    (x = 0 .. N_x-1).  With pressure ends, columns 0 and N_x-1 are the
+ *    inlet and outlet boundary columns and columns 1 .. N_x-2 are updated.
+ *  - Host arrays laid out [row][column] hold N*N_x doubles; population arrays
+ *    are [species][i][row][column] (2*9*N*N_x floats), species a first,
+ *    velocities c_0..c_8 = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),
+ *    (-1,-1),(1,-1).
+ *  - Every function returns LBM_OK (0) or a negative LBM_E* code and, on
+ *    error, sets a thread-local message readable with lbm_mix_last_error().
+ *  - A handle is used by one host thread at a time.  Work is enqueued on the
+ *    handle's CUDA stream; getters synchronise that stream, lbm_mix_step
+ *    does not.
+ */
+#ifndef LBM_MIX_H
+#define LBM_MIX_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_EINVAL (-1)         /* bad argument or parameter */
+#define LBM_ENOMEM (-2)         /* device or host allocation failed */
+#define LBM_ECUDA (-3)          /* CUDA runtime error (message has details) */
+#define LBM_ENONFINITE (-4)     /* a non-finite density or mass appeared */
+#define LBM_ENOTCONVERGED (-5)  /* run_to_steady hit max_steps */
+#define LBM_ETIMEOUT (-6)       /* reserved: a bounded device wait expired */
+
+#define LBM_FP32 0 /* population storage: FP32 */
+
+typedef struct lbm_mix lbm_mix; /* opaque, owned by the library */
+
+/* Physical problem (Sec. 2, Table 1) and model knobs (Sec. 3). */
+typedef struct {
+  double m_a, m_b;      /* molecular masses, any common unit, > 0 */
+  double C_l;           /* light-species mole fraction at the inlet, (0,1) */
+  double C_l_out;       /* at the outlet; < 0 means equal to C_l */
+  double theta;         /* P_in / P_out >= 1 */
+  double Kn_out;        /* lambda_out / H > 0 */
+  int N;                /* lattice cells across H, >= 2 */
+  int N_x;              /* lattice columns; <= 0 means round(N * L_over_H) */
+  double L_over_H;      /* channel aspect ratio, used when N_x <= 0 */
+  double accommodation; /* uniform wall accommodation alpha in (0,1] (Eq. A12) */
+  double c_m0;          /* velocity slip coefficient at alpha = 1 (Eq. R);
+                           scaled by (2 - alpha)/alpha per wall node */
+  double tau_rho, tau_e, tau_eps; /* fixed relaxation times (Sec. 3.3) */
+  double mu_ratio_a, mu_ratio_b;  /* mu_sigma / mu of the mixture */
+  int storage;          /* LBM_FP32 */
+  int x_periodic;       /* 1: periodic in x instead of pressure ends */
+} lbm_mix_params;
+
+/* Fills the defaults: He-Ar (4.003, 39.948), C_l = 0.5, C_l_out = -1,
+ * theta = 2, Kn_out = 0.1, N = 16, N_x = 0, L_over_H = 20, alpha = 1,
+ * c_m0 = 1.016, tau_rho = 1, tau_e = 1.1, tau_eps = 1.2, mu ratios 1,
+ * LBM_FP32, x_periodic = 0.  NULL-safe. */
+void lbm_mix_default_params(lbm_mix_params* p);
+
+/* Validates p, derives the lattice constants (Eqs. P, EQFrb, rho2 with the
+ * outlet mean free path Kn_out * N), allocates the two population buffers
+ * and the reduction buffers on the current CUDA device and returns a handle
+ * in *out.  stream: a cudaStream_t to enqueue on, or NULL for a stream owned
+ * by the handle.  No device work is done besides allocation.  Parameters are
+ * checked before any CUDA call, so LBM_EINVAL needs no GPU.  Errors:
+ * LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA; *out is NULL on error. */
+int lbm_mix_create(const lbm_mix_params* p, void* stream, lbm_mix** out);
+
+/* Releases every resource of h. NULL-safe. */
+void lbm_mix_destroy(lbm_mix* h);
+
+/* Initial state: pressure linear from theta * p_out (column 0) to p_out
+ * (column N_x-1), zero velocity, light mole fraction linear from C_l to
+ * C_l_out, populations at equilibrium (Eq. feq).  Resets the step count. */
+int lbm_mix_init(lbm_mix* h);
+
+/* Advances nsteps >= 0 time steps (Eq. MRT), one fused collide-stream pass
+ * per step on the handle's stream, asynchronously.  Each pass also reduces
+ * the separation diagnostics of the new state in FP64. */
+int lbm_mix_step(lbm_mix* h, long nsteps);
+
+/* Steps in blocks of `check_every` (>= 1) until the steady-state residual
+ * R = |c(t) - c(t-K)|_2 / (K |c(t)|_2) of the column-integrated species
+ * densities and x mass flows c drops to tol, or max_steps are taken
+ * (LBM_ENOTCONVERGED), or a non-finite value appears (LBM_ENONFINITE).
+ * steps_out / residual_out (nullable) receive the steps taken and final R. */
+int lbm_mix_run_to_steady(lbm_mix* h, double tol, long max_steps, long check_every,
+                          long* steps_out, double* residual_out);
+
+/* Macroscopic fields of the current state, FP64 host arrays [N][N_x], each
+ * nullable: species densities and the species velocities of Eq. rhou,
+ * rho_s u_s = (2 tau_d - 1)/(2 tau_d) sum_i c_i f_si + rho_s u / (2 tau_d).
+ * Columns 0 and N_x-1 (pressure ends) hold rho_s = kappa_s (2 rho_s(1) -
+ * rho_s(2)) with the density-correction factor of Eq. rho2, and
+ * u_s = 2 u_s(1) - u_s(2).  Synchronises. */
+int lbm_mix_moments(lbm_mix* h, double* rho_a, double* rho_b, double* ua_x, double* ua_y,
+                    double* ub_x, double* ub_y);
+
+/* Same fields written to caller-owned DEVICE memory d_out[6][N][N_x]
+ * (rho_a, rho_b, ua_x, ua_y, ub_x, ub_y); enqueued, not synchronised. */
+int lbm_mix_moments_device(lbm_mix* h, double* d_out);
+
+/* Separation diagnostics of the current state (Eqs. C, CL, Clline), each
+ * nullable: CL = (C_l,in - min_x C_l(x)) / C_l,in over the updated columns,
+ * with C_l(x) = sum_j n_l / sum_j (n_a + n_b); C~_l over all N_x columns
+ * (boundary columns at their imposed values); mdot_s = mean over updated
+ * columns of sum_j rho_s u_s,x; Cl_profile receives N_x values; x_min the
+ * column of the minimum.  Synchronises; LBM_ENONFINITE if the state holds a
+ * non-finite value. */
+int lbm_mix_separation(lbm_mix* h, double* CL, double* Cl_tilde, double* mdot_a,
+                       double* mdot_b, double* Cl_profile, int* x_min);
+
+/* Copies up to max_records of the most recent per-step diagnostic records,
+ * oldest first, into rec[max_records][8] = {step, CL, C~_l, mdot_a, mdot_b,
+ * x_min, total mass a, total mass b}; *count gets the number copied.  The
+ * library keeps the last 4096 steps.  Synchronises. */
+int lbm_mix_history(lbm_mix* h, double* rec, long max_records, long* count);
+
+/* Per-wall-node accommodation coefficients alpha in (0,1] (Eq. A12):
+ * n = 2*N_x values, bottom wall then top wall, host FP64. */
+int lbm_mix_set_accommodation_field(lbm_mix* h, const double* alpha, long n);
+
+/* Replaces the state by caller post-collision populations (host FP32,
+ * [2][9][N][N_x], n = 18*N*N_x); the next step streams them.  Resets the
+ * step count; until the next step, lbm_mix_moments reports the moments of
+ * these populations themselves. */
+int lbm_mix_set_post_state(lbm_mix* h, const float* f, long n);
+
+/* Copies the current post-collision populations to host FP32 [2][9][N][N_x].
+ * Synchronises. */
+int lbm_mix_get_post_state(lbm_mix* h, float* f, long n);
+
+/* Lattice size and steps taken since init / set_post_state. */
+int lbm_mix_dims(const lbm_mix* h, int* N, int* N_x, long* steps);
+
+/* Waits for all work enqueued on the handle's stream. */
+int lbm_mix_sync(lbm_mix* h);
+
+/* Device evaluation (FP32) of the exponential integral E_1 = E_i of Eq. psi
+ * and of psi itself at n host points x[] (> 0); writes e1[] and psi[]
+ * (nullable).  Diagnostic entry point for testing the device special
+ * functions; uses its own temporary device memory. */
+int lbm_mix_eval_special(const double* x, double* e1, double* psi, long n);
+
+/* Static description of an error code; never NULL. */
+const char* lbm_mix_strerror(int status);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* lbm_mix_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_MIX_H */

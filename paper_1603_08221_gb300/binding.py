@@ -1,0 +1,311 @@
+"""ctypes binding of the C ABI declared in include/lbm_mix.h.
+
+Argument marshalling only: every function here forwards to the function of
+the same name in ``liblbm_mix.so`` (sm_103a CUDA).  There is no CPU path; if
+the library has not been built, loading raises.  Streams may be given as
+integers (``torch.cuda.Stream.cuda_stream``) or objects with a
+``cuda_stream`` attribute.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm_mix.so")
+
+LBM_OK = 0
+LBM_EINVAL = -1
+LBM_ENOMEM = -2
+LBM_ECUDA = -3
+LBM_ENONFINITE = -4
+LBM_ENOTCONVERGED = -5
+LBM_ETIMEOUT = -6
+LBM_FP32 = 0
+
+
+class lbm_mix_params(ctypes.Structure):
+    _fields_ = [
+        ("m_a", ctypes.c_double), ("m_b", ctypes.c_double),
+        ("C_l", ctypes.c_double), ("C_l_out", ctypes.c_double),
+        ("theta", ctypes.c_double), ("Kn_out", ctypes.c_double),
+        ("N", ctypes.c_int), ("N_x", ctypes.c_int),
+        ("L_over_H", ctypes.c_double),
+        ("accommodation", ctypes.c_double), ("c_m0", ctypes.c_double),
+        ("tau_rho", ctypes.c_double), ("tau_e", ctypes.c_double),
+        ("tau_eps", ctypes.c_double),
+        ("mu_ratio_a", ctypes.c_double), ("mu_ratio_b", ctypes.c_double),
+        ("storage", ctypes.c_int), ("x_periodic", ctypes.c_int),
+    ]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, func: str, message: str):
+        super().__init__(f"{func}: {message} (status {status})")
+        self.status = status
+
+
+_D = ctypes.c_double
+_PD = ctypes.POINTER(ctypes.c_double)
+_PF = ctypes.POINTER(ctypes.c_float)
+_H = ctypes.c_void_p
+_I = ctypes.c_int
+_L = ctypes.c_long
+
+_SIGS = {
+    "lbm_mix_default_params": (None, [ctypes.POINTER(lbm_mix_params)]),
+    "lbm_mix_create": (_I, [ctypes.POINTER(lbm_mix_params), ctypes.c_void_p,
+                            ctypes.POINTER(ctypes.c_void_p)]),
+    "lbm_mix_destroy": (None, [_H]),
+    "lbm_mix_init": (_I, [_H]),
+    "lbm_mix_step": (_I, [_H, _L]),
+    "lbm_mix_run_to_steady": (_I, [_H, _D, _L, _L, ctypes.POINTER(_L), _PD]),
+    "lbm_mix_moments": (_I, [_H, _PD, _PD, _PD, _PD, _PD, _PD]),
+    "lbm_mix_moments_device": (_I, [_H, ctypes.c_void_p]),
+    "lbm_mix_separation": (_I, [_H, _PD, _PD, _PD, _PD, _PD, ctypes.POINTER(_I)]),
+    "lbm_mix_history": (_I, [_H, _PD, _L, ctypes.POINTER(_L)]),
+    "lbm_mix_set_accommodation_field": (_I, [_H, _PD, _L]),
+    "lbm_mix_set_post_state": (_I, [_H, _PF, _L]),
+    "lbm_mix_get_post_state": (_I, [_H, _PF, _L]),
+    "lbm_mix_dims": (_I, [_H, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_L)]),
+    "lbm_mix_sync": (_I, [_H]),
+    "lbm_mix_eval_special": (_I, [_PD, _PD, _PD, _L]),
+    "lbm_mix_strerror": (ctypes.c_char_p, [_I]),
+    "lbm_mix_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads liblbm_mix.so; raises if it is missing (no fallback exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(
+                f"{path} is missing: build the CUDA library first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status: int, func: str):
+    if status != LBM_OK:
+        msg = _lib.lbm_mix_last_error().decode() or _lib.lbm_mix_strerror(status).decode()
+        raise LbmError(status, func, msg)
+
+
+def _dptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_PD)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+# ------------------------------------------------ same-name thin wrappers
+def lbm_mix_default_params() -> lbm_mix_params:
+    p = lbm_mix_params()
+    load().lbm_mix_default_params(ctypes.byref(p))
+    return p
+
+
+def lbm_mix_create(params: lbm_mix_params, stream=None) -> int:
+    lib = load()
+    h = ctypes.c_void_p()
+    _check(lib.lbm_mix_create(ctypes.byref(params), _stream_handle(stream), ctypes.byref(h)),
+           "lbm_mix_create")
+    return h.value
+
+
+def lbm_mix_destroy(h) -> None:
+    load().lbm_mix_destroy(h)
+
+
+def lbm_mix_init(h) -> None:
+    _check(load().lbm_mix_init(h), "lbm_mix_init")
+
+
+def lbm_mix_step(h, nsteps: int) -> None:
+    _check(load().lbm_mix_step(h, int(nsteps)), "lbm_mix_step")
+
+
+def lbm_mix_run_to_steady(h, tol: float, max_steps: int, check_every: int):
+    steps = _L()
+    res = _D()
+    st = load().lbm_mix_run_to_steady(h, float(tol), int(max_steps), int(check_every),
+                                      ctypes.byref(steps), ctypes.byref(res))
+    if st not in (LBM_OK, LBM_ENOTCONVERGED):
+        _check(st, "lbm_mix_run_to_steady")
+    return st, steps.value, res.value
+
+
+def lbm_mix_dims(h):
+    N, Nx, steps = _I(), _I(), _L()
+    _check(load().lbm_mix_dims(h, ctypes.byref(N), ctypes.byref(Nx), ctypes.byref(steps)),
+           "lbm_mix_dims")
+    return N.value, Nx.value, steps.value
+
+
+def lbm_mix_moments(h) -> dict:
+    N, Nx, _ = lbm_mix_dims(h)
+    outs = [np.empty((N, Nx)) for _ in range(6)]
+    _check(load().lbm_mix_moments(h, *[_dptr(o) for o in outs]), "lbm_mix_moments")
+    return dict(zip(["rho_a", "rho_b", "ua_x", "ua_y", "ub_x", "ub_y"], outs))
+
+
+def lbm_mix_moments_device(h, d_out_ptr: int) -> None:
+    _check(load().lbm_mix_moments_device(h, ctypes.c_void_p(int(d_out_ptr))),
+           "lbm_mix_moments_device")
+
+
+def lbm_mix_separation(h) -> dict:
+    _, Nx, _ = lbm_mix_dims(h)
+    CL, Ct, ma, mb = _D(), _D(), _D(), _D()
+    xm = _I()
+    prof = np.empty(Nx)
+    _check(load().lbm_mix_separation(h, ctypes.byref(CL), ctypes.byref(Ct), ctypes.byref(ma),
+                                     ctypes.byref(mb), _dptr(prof), ctypes.byref(xm)),
+           "lbm_mix_separation")
+    return dict(CL=CL.value, Cl_tilde=Ct.value, mdot_a=ma.value, mdot_b=mb.value,
+                Cl_profile=prof, x_min=xm.value)
+
+
+def lbm_mix_history(h, max_records: int = 4096) -> np.ndarray:
+    rec = np.zeros((max_records, 8))
+    cnt = _L()
+    _check(load().lbm_mix_history(h, _dptr(rec), int(max_records), ctypes.byref(cnt)),
+           "lbm_mix_history")
+    return rec[:cnt.value]
+
+
+def lbm_mix_set_accommodation_field(h, alpha: np.ndarray) -> None:
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    _check(load().lbm_mix_set_accommodation_field(h, _dptr(a), a.size),
+           "lbm_mix_set_accommodation_field")
+
+
+def lbm_mix_set_post_state(h, f: np.ndarray) -> None:
+    a = np.ascontiguousarray(f, dtype=np.float32)
+    _check(load().lbm_mix_set_post_state(h, a.ctypes.data_as(_PF), a.size),
+           "lbm_mix_set_post_state")
+
+
+def lbm_mix_get_post_state(h) -> np.ndarray:
+    N, Nx, _ = lbm_mix_dims(h)
+    out = np.empty((2, 9, N, Nx), dtype=np.float32)
+    _check(load().lbm_mix_get_post_state(h, out.ctypes.data_as(_PF), out.size),
+           "lbm_mix_get_post_state")
+    return out
+
+
+def lbm_mix_sync(h) -> None:
+    _check(load().lbm_mix_sync(h), "lbm_mix_sync")
+
+
+def lbm_mix_eval_special(x: np.ndarray):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    e1 = np.empty_like(x)
+    ps = np.empty_like(x)
+    _check(load().lbm_mix_eval_special(_dptr(x), _dptr(e1), _dptr(ps), x.size),
+           "lbm_mix_eval_special")
+    return e1, ps
+
+
+def lbm_mix_strerror(status: int) -> str:
+    return load().lbm_mix_strerror(int(status)).decode()
+
+
+def lbm_mix_last_error() -> str:
+    return load().lbm_mix_last_error().decode()
+
+
+# --------------------------------------------------------- convenience
+def make_params(**kw) -> lbm_mix_params:
+    """Default parameters updated from keyword arguments (names of the C
+    struct; ``L_over_H`` or ``N_x`` select the length)."""
+    p = lbm_mix_default_params()
+    names = {f[0] for f in lbm_mix_params._fields_}
+    for k, v in kw.items():
+        if k not in names:
+            raise KeyError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+class LbmMix:
+    """Owns one handle; methods forward to the same-name C functions."""
+
+    def __init__(self, stream=None, **params):
+        self.params = make_params(**params)
+        self.h = lbm_mix_create(self.params, stream)
+        self.N, self.N_x, _ = lbm_mix_dims(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_mix_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init(self):
+        lbm_mix_init(self.h)
+
+    def step(self, n: int = 1):
+        lbm_mix_step(self.h, n)
+
+    def sync(self):
+        lbm_mix_sync(self.h)
+
+    @property
+    def steps(self) -> int:
+        return lbm_mix_dims(self.h)[2]
+
+    def moments(self) -> dict:
+        return lbm_mix_moments(self.h)
+
+    def separation(self) -> dict:
+        return lbm_mix_separation(self.h)
+
+    def history(self, max_records: int = 4096) -> np.ndarray:
+        return lbm_mix_history(self.h, max_records)
+
+    def set_accommodation_field(self, alpha):
+        lbm_mix_set_accommodation_field(self.h, alpha)
+
+    def set_post_state(self, f):
+        lbm_mix_set_post_state(self.h, f)
+
+    def get_post_state(self) -> np.ndarray:
+        return lbm_mix_get_post_state(self.h)
+
+    def run_to_steady(self, tol: float, max_steps: int, check_every: int = 100):
+        return lbm_mix_run_to_steady(self.h, tol, max_steps, check_every)

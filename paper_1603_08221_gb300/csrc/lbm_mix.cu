@@ -1,0 +1,1283 @@
+// lbm_mix.cu — sm_103a implementation of the C ABI in include/lbm_mix.h.
+//
+// One time step of the two-species D2Q9 MRT lattice Boltzmann model of
+// Wang, Xu & Guo (arXiv:1603.08221, Sec. 3) is ONE kernel launch
+// (lbm_step_kernel): pull-streaming from the previous post-collision buffer
+// with the diffuse-bounce-back walls (Eqs. bot, bot2, R) and the
+// extrapolation-correction ends (Eqs. rho1, rho2) folded into the loads,
+// moments (Eq. rhou), effective relaxation times (Eqs. EQFrb, EQFrsp, psi,
+// taos, taoq, A12), the MRT collision (Eqs. MR, m, S, feq) for both species,
+// the store of the new post-collision buffer, and FP64 per-column reductions
+// that feed the next step's density correction and the separation
+// diagnostics (Eqs. C, CL, Clline).
+//
+// Data layout in HBM (per buffer): f[species][i][row][column], FP32, row
+// pitch padded to 32 floats (128 B); two buffers A/B alternate.  One CTA owns
+// a strip of 32 columns over ALL rows, sweeping rows in steps of TY, so that
+// every per-column quantity (the tau_q of the two walls, the column sums) is
+// produced inside one CTA without atomics and in a fixed order.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/lbm_mix.h"
+
+namespace {
+
+// ---------------------------------------------------------------- errors
+thread_local char g_err[512] = "";
+
+int set_err(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int set_err(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return set_err(LBM_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                     __FILE__, __LINE__);                                             \
+  } while (0)
+
+// ------------------------------------------------------- lattice constants
+constexpr int TX = 32;          // columns per CTA (one warp per row segment)
+constexpr int TY = 8;           // rows per sweep iteration
+constexpr int NPART = 8;        // doubles per CTA partial
+constexpr int NREC = 8;         // doubles per diagnostic record
+constexpr int DIAG_CAP = 4096;  // diagnostic records kept
+constexpr float kPi = 3.14159265358979323846f;
+
+struct Lat {
+  int N, Nx, pitch;
+  unsigned pop_stride;   // N * pitch
+  unsigned spec_stride;  // 9 * pop_stride
+  int x_periodic;
+  int light;             // index of the light species
+  float s[2];            // s_sigma = m_min / m_sigma
+  float inv_c_lam;       // 1 / (3 mu sqrt(pi/6))
+  float c_lam;           // 3 mu sqrt(pi/6): lambda = c_lam / (n sqrt(m_x))
+  float c_xl[2];         // 3 mu_s sqrt(pi/(6 m_s)): x_s lambda_s = c_xl / n
+  float inv_c_xl[2];
+  float c_ts;            // sqrt(6/pi)
+  float c_td;            // (3/2) sqrt(3 m0 m_a m_b / m_min)
+  float om_e, om_eps;    // 1/tau_e, 1/tau_eps
+  float c_m0;
+  float H;               // channel height = N
+  double mh[2];          // m_sigma / m_min
+  double rho_in[2], rho_out[2];
+  double C_in, C_out;    // light-species mole fraction at the ends
+};
+
+// ------------------------------------------------------ special functions
+// E_1(x) for 0 < x <= 1 from its convergent series (Abramowitz & Stegun
+// 5.1.11) truncated after ten terms (remainder < 2.3e-9 at x = 1):
+// E_1(x) = -gamma - ln x + sum_{k=1}^{10} (-1)^{k+1} x^k / (k k!).
+__device__ __forceinline__ float e1_series(float x) {
+  float p = -1.0f / 36288000.0f;
+  p = fmaf(p, x, 1.0f / 3265920.0f);
+  p = fmaf(p, x, -1.0f / 322560.0f);
+  p = fmaf(p, x, 1.0f / 35280.0f);
+  p = fmaf(p, x, -1.0f / 4320.0f);
+  p = fmaf(p, x, 1.0f / 600.0f);
+  p = fmaf(p, x, -1.0f / 96.0f);
+  p = fmaf(p, x, 1.0f / 18.0f);
+  p = fmaf(p, x, -0.25f);
+  p = fmaf(p, x, 1.0f);
+  return fmaf(p, x, -0.5772156649f) - logf(x);
+}
+
+// x e^x E_1(x) for x >= 1: Hastings' rational approximation as tabulated in
+// Abramowitz & Stegun 5.1.56 (absolute error < 2e-8).
+__device__ __forceinline__ float xexe1_rational(float x) {
+  float num = (((x + 8.5733287401f) * x + 18.0590169730f) * x + 8.6347608925f) * x +
+              0.2677737343f;
+  float den = (((x + 9.5733223454f) * x + 25.6329561486f) * x + 21.0996530827f) * x +
+              3.9584969228f;
+  return num / den;
+}
+
+__device__ __forceinline__ float e1_dev(float x) {
+  return x <= 1.0f ? e1_series(x) : expf(-x) * xexe1_rational(x) / x;
+}
+
+// psi(a) = 1 + (a - 1) e^{-a} - a^2 E_1(a)  (Eq. psi), written without
+// cancellation: for a <= 1 as (1 - e^{-a}) + a e^{-a} - a^2 E_1(a), for
+// a > 1 as 1 + e^{-a} [(a - 1) - a (x e^x E_1)(a)].
+__device__ __forceinline__ float psi_dev(float a) {
+  if (a <= 1.0f) {
+    if (!(a > 0.0f)) return 0.0f;
+    float em1 = expm1f(-a);
+    return fmaf(a, 1.0f + em1, -em1) - a * a * e1_series(a);
+  }
+  float e = expf(-a);
+  return fmaf(e, (a - 1.0f) - a * xexe1_rational(a), 1.0f);
+}
+
+// psi'(a) = 2 e^{-a} - 2 a E_1(a).
+__device__ __forceinline__ float dpsi_dev(float a) {
+  if (a <= 1.0f) {
+    if (!(a > 0.0f)) return 2.0f;
+    return 2.0f * expf(-a) - 2.0f * a * e1_series(a);
+  }
+  return 2.0f * expf(-a) * (1.0f - xexe1_rational(a));
+}
+
+// ------------------------------------------------------------- streaming
+struct Ends {
+  float kin[2], kout[2];  // Eq. rho2 density-correction factors
+};
+
+__device__ __forceinline__ float ld(const float* __restrict__ f, const Lat& L, int sp, int i,
+                                    int j, int x) {
+  return __ldg(f + sp * L.spec_stride + i * L.pop_stride + j * L.pitch + x);
+}
+
+// Post-collision value that population i carries into column x from its
+// upstream neighbour column xs at row js; the inlet/outlet ghost columns
+// (Eq. rho1, all nine populations extrapolated and scaled by Eq. rho2) are
+// virtual.
+__device__ __forceinline__ float src(const float* __restrict__ f, const Lat& L, const Ends& E,
+                                     int sp, int i, int js, int xs) {
+  if (!L.x_periodic) {
+    if (xs == 0)
+      return E.kin[sp] * (2.0f * ld(f, L, sp, i, js, 1) - ld(f, L, sp, i, js, 2));
+    if (xs == L.Nx - 1)
+      return E.kout[sp] *
+             (2.0f * ld(f, L, sp, i, js, L.Nx - 2) - ld(f, L, sp, i, js, L.Nx - 3));
+  }
+  return ld(f, L, sp, i, js, xs);
+}
+
+// Pre-collision populations of node (x, j): f_i(x) = f'_i(x - c_i) (Eq. MRT),
+// with the unknown populations of the wall rows from diffuse bounce-back
+// (Eqs. bot, bot2) using the post-collision state of the same node: the wall
+// equilibrium f^eq_i(rho_w, u_w = 0) = w_i rho_w s with rho_w from zero normal
+// species flux, i.e. f^eq_i = 6 w_i (sum of the outgoing f').
+__device__ __forceinline__ void pull_node(const float* __restrict__ f, const Lat& L,
+                                          const Ends& E, int x, int j, float r_bot,
+                                          float r_top, float fs[2][9]) {
+  int xm = x - 1, xp = x + 1;
+  if (L.x_periodic) {
+    if (xm < 0) xm += L.Nx;
+    if (xp >= L.Nx) xp -= L.Nx;
+  }
+  const bool bot = (j == 0), top = (j == L.N - 1);
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    float* g = fs[sp];
+    g[0] = ld(f, L, sp, 0, j, x);
+    g[1] = src(f, L, E, sp, 1, j, xm);
+    g[3] = src(f, L, E, sp, 3, j, xp);
+    if (bot) {
+      float o4 = ld(f, L, sp, 4, j, x), o7 = ld(f, L, sp, 7, j, x), o8 = ld(f, L, sp, 8, j, x);
+      float t = r_bot * (o4 + o7 + o8), q = 1.0f - r_bot;
+      g[2] = fmaf(q, o4, t * (2.0f / 3.0f));
+      g[5] = fmaf(q, o7, t * (1.0f / 6.0f));
+      g[6] = fmaf(q, o8, t * (1.0f / 6.0f));
+    } else {
+      g[2] = ld(f, L, sp, 2, j - 1, x);
+      g[5] = src(f, L, E, sp, 5, j - 1, xm);
+      g[6] = src(f, L, E, sp, 6, j - 1, xp);
+    }
+    if (top) {
+      float o2 = ld(f, L, sp, 2, j, x), o5 = ld(f, L, sp, 5, j, x), o6 = ld(f, L, sp, 6, j, x);
+      float t = r_top * (o2 + o5 + o6), q = 1.0f - r_top;
+      g[4] = fmaf(q, o2, t * (2.0f / 3.0f));
+      g[7] = fmaf(q, o5, t * (1.0f / 6.0f));
+      g[8] = fmaf(q, o6, t * (1.0f / 6.0f));
+    } else {
+      g[4] = ld(f, L, sp, 4, j + 1, x);
+      g[7] = src(f, L, E, sp, 7, j + 1, xp);
+      g[8] = src(f, L, E, sp, 8, j + 1, xm);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- moments
+struct Macro {
+  float rho[2], jx[2], jy[2];
+  float ux, uy;
+  float inv_n, mx;
+};
+
+__device__ __forceinline__ void macro(const Lat& L, const float fs[2][9], Macro& m) {
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    const float* g = fs[sp];
+    m.rho[sp] = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    m.jx[sp] = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+    m.jy[sp] = (g[2] - g[4]) + (g[5] - g[7]) + (g[6] - g[8]);
+  }
+  float rho = m.rho[0] + m.rho[1];
+  float inv_rho = 1.0f / rho;
+  m.ux = (m.jx[0] + m.jx[1]) * inv_rho;
+  m.uy = (m.jy[0] + m.jy[1]) * inv_rho;
+  float n = fmaf(m.rho[0], L.s[0], m.rho[1] * L.s[1]);  // number density (Eq. P)
+  m.inv_n = 1.0f / n;
+  m.mx = rho * m.inv_n;  // m_x = rho / n
+}
+
+// Wall-confinement factor Psi(y) = (psi(y/lambda) + psi((H-y)/lambda))/2.
+__device__ __forceinline__ float Psi_dev(float y, float H, float inv_lam) {
+  return 0.5f * (psi_dev(y * inv_lam) + psi_dev((H - y) * inv_lam));
+}
+
+// tau_s (Eq. taos) and tau_d (Eq. EQFrsp with lambda_se = lambda_s Psi(y;
+// lambda_s), lambda_s = (mu_s/p_s) sqrt(pi k_B T/(2 m_s)), p_s = x_s p).
+__device__ __forceinline__ void taus(const Lat& L, const Macro& m, float y, float& tau_s,
+                                     float& tau_d) {
+  float rs_mx = rsqrtf(m.mx);
+  float lam = L.c_lam * m.inv_n * rs_mx;
+  float inv_lam = L.inv_c_lam * (1.0f / (m.inv_n * rs_mx));
+  tau_s = 0.5f + lam * Psi_dev(y, L.H, inv_lam) * L.c_ts * rs_mx;
+  float br = 0.0f;
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    float n_s = m.rho[sp] * L.s[sp];
+    float inv_lam_s = n_s * L.inv_c_xl[sp];          // 1 / lambda_s
+    float xl_e = L.c_xl[sp] * m.inv_n * Psi_dev(y, L.H, inv_lam_s);  // x_s lambda_se
+    br += rsqrtf(xl_e);
+  }
+  tau_d = 0.5f + L.c_td / (m.mx * br * br);
+}
+
+// tau_q of Eq. taoq from the wall node's lambda and m_x (tau'_s(0) in its
+// last term, dx = 1) and the node's accommodation coefficient (Eq. A12).
+__device__ __forceinline__ float tau_q_wall(const Lat& L, const Macro& m, float alpha) {
+  const float vs = 0.72360125455f;  // varsigma = sqrt(pi/6)
+  float rs_mx = rsqrtf(m.mx);
+  float lam = L.c_lam * m.inv_n * rs_mx;
+  float g = L.c_ts * rs_mx;  // sqrt(6/(pi m_x))
+  float a = L.H / lam;
+  float tt = lam * 0.5f * psi_dev(a) * g;
+  float dtt = 0.5f * g * (2.0f - dpsi_dev(a));
+  float A1 = (2.0f - alpha) / alpha * (1.0f - 0.1817f * alpha);
+  float A2 = 1.0f / kPi + 0.5f * A1 * A1;
+  return 0.5f + (3.0f + 24.0f * vs * vs * tt * tt * A2) / (16.0f * tt) +
+         dtt * (12.0f + 30.0f * tt * vs * A1) / (16.0f * tt * tt);
+}
+
+// r of Eq. R (first printed form) from the mixture molecular mass of the
+// reflected post-collision state at the wall node, c_m = c_m0 (2-alpha)/alpha.
+__device__ __forceinline__ float dbb_r(const Lat& L, const float* __restrict__ f, int x, int j,
+                                       float alpha) {
+  float rho[2];
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) acc += ld(f, L, sp, i, j, x);
+    rho[sp] = acc;
+  }
+  float mx = (rho[0] + rho[1]) / fmaf(rho[0], L.s[0], rho[1] * L.s[1]);
+  float cm = L.c_m0 * (2.0f - alpha) / alpha;
+  return 2.0f - 2.0f / (1.0f + cm * sqrtf(kPi * mx / 6.0f));
+}
+
+// MRT collision of one species (Eqs. MR, S, feq) in moment space:
+// f' = f - M^{-1} S (m - m^eq) with M^{-1} = M^T diag(1/9, 1/36, 1/36, 1/6,
+// 1/12, 1/6, 1/12, 1/4, 1/4) and the closed-form equilibrium moments
+// m^eq = rho_s (1, -4 + 2s + 3u^2, 4 - 3s - 3u^2, u_x, -u_x, u_y, -u_y,
+// u_x^2 - u_y^2, u_x u_y).  Returns the x component of the species momentum
+// of Eq. rhou, j_x - (j_x - rho_s u_x)/(2 tau_d).
+__device__ __forceinline__ float collide(float g[9], float rho, float s, float ux, float uy,
+                                         float om_e, float om_eps, float om_d, float om_q,
+                                         float om_s) {
+  float u2 = ux * ux + uy * uy;
+  float a14 = (g[1] + g[2]) + (g[3] + g[4]);
+  float a58 = (g[5] + g[6]) + (g[7] + g[8]);
+  float e = fmaf(-4.0f, g[0], fmaf(2.0f, a58, -a14));
+  float eps = fmaf(4.0f, g[0], fmaf(-2.0f, a14, a58));
+  float jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+  float jy = (g[2] - g[4]) + (g[5] - g[7]) + (g[6] - g[8]);
+  float dx56 = (g[5] - g[6]) + (g[8] - g[7]);  // jx part of the diagonals
+  float dy56 = (g[5] - g[7]) + (g[6] - g[8]);
+  float qx = fmaf(2.0f, g[3] - g[1], dx56);
+  float qy = fmaf(2.0f, g[4] - g[2], dy56);
+  float pxx = (g[1] + g[3]) - (g[2] + g[4]);
+  float pxy = (g[5] + g[7]) - (g[6] + g[8]);
+  float de = om_e * (e - rho * (-4.0f + 2.0f * s + 3.0f * u2));
+  float deps = om_eps * (eps - rho * (4.0f - 3.0f * s - 3.0f * u2));
+  float djx = om_d * (jx - rho * ux);
+  float djy = om_d * (jy - rho * uy);
+  float dqx = om_q * (qx + rho * ux);
+  float dqy = om_q * (qy + rho * uy);
+  float dpxx = om_s * (pxx - rho * (ux * ux - uy * uy));
+  float dpxy = om_s * (pxy - rho * ux * uy);
+  float c0 = (de - deps) * (1.0f / 9.0f);
+  float c14 = de * (1.0f / 36.0f) + deps * (1.0f / 18.0f);
+  float c58 = -(de * (1.0f / 18.0f) + deps * (1.0f / 36.0f));
+  float ax = (dqx - djx) * (1.0f / 6.0f), ay = (dqy - djy) * (1.0f / 6.0f);
+  float bx = -(djx * (1.0f / 6.0f) + dqx * (1.0f / 12.0f));
+  float by = -(djy * (1.0f / 6.0f) + dqy * (1.0f / 12.0f));
+  float pp = dpxx * 0.25f, pq = dpxy * 0.25f;
+  g[0] += c0;
+  g[1] += c14 + ax - pp;
+  g[2] += c14 + ay + pp;
+  g[3] += c14 - ax - pp;
+  g[4] += c14 - ay + pp;
+  g[5] += c58 + bx + by - pq;
+  g[6] += c58 - bx + by + pq;
+  g[7] += c58 - bx - by - pq;
+  g[8] += c58 + bx - by + pq;
+  return jx - 0.5f * djx;
+}
+
+// Density-correction factors of Eq. rho2 for the ghost columns, from the
+// column sums of the state being streamed; only the CTAs that own column 1
+// or column N_x - 2 read them.
+__device__ __forceinline__ Ends load_ends(const Lat& L, const double* __restrict__ cs) {
+  Ends E;
+  E.kin[0] = E.kin[1] = E.kout[0] = E.kout[1] = 1.0f;
+  if (L.x_periodic) return E;
+  const int Nx = L.Nx, x0 = blockIdx.x * TX;
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    const double* c = cs + (size_t)sp * Nx;
+    if (x0 <= 1 && 1 < x0 + TX) E.kin[sp] = (float)(L.N * L.rho_in[sp] / (2.0 * c[1] - c[2]));
+    if (x0 <= Nx - 2 && Nx - 2 < x0 + TX)
+      E.kout[sp] = (float)(L.N * L.rho_out[sp] / (2.0 * c[Nx - 2] - c[Nx - 3]));
+  }
+  return E;
+}
+
+__device__ __forceinline__ bool interior(const Lat& L, int x) {
+  return L.x_periodic ? (x < L.Nx) : (x >= 1 && x <= L.Nx - 2);
+}
+
+// Per-CTA wall data for the strip: r (both walls), 1/tau_q (both walls).
+struct WallSmem {
+  float r[2][TX];
+  float om_q[2][TX];
+};
+
+// Prologue of the step and moments kernels: warp ty = 0 handles the bottom
+// wall node of each column of the strip, warp ty = 1 the top one.
+template <bool WITH_TQ>
+__device__ __forceinline__ void wall_prologue(const Lat& L, const float* __restrict__ fin,
+                                              const float* __restrict__ alpha, const Ends& E,
+                                              int x, WallSmem& sm) {
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  if (ty < 2) {
+    float r = 1.0f, omq = 1.0f;
+    if (interior(L, x)) {
+      const int jw = ty == 0 ? 0 : L.N - 1;
+      float al = alpha[ty * L.Nx + x];
+      r = dbb_r(L, fin, x, jw, al);
+      if (WITH_TQ) {
+        float fs[2][9];
+        pull_node(fin, L, E, x, jw, r, r, fs);
+        Macro m;
+        macro(L, fs, m);
+        omq = 1.0f / tau_q_wall(L, m, al);
+      }
+    }
+    sm.r[ty][tx] = r;
+    sm.om_q[ty][tx] = omq;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------ step kernel
+struct StepArgs {
+  const float* __restrict__ fin;  // post-collision state of step t-1
+  float* __restrict__ fout;       // post-collision state of step t
+  const double* __restrict__ cs_in;  // [4][Nx] column sums of the state in fin
+  double* __restrict__ cs_out;       // [4][Nx] column sums of the state of step t
+  const float* __restrict__ alpha;   // [2][Nx]
+  double* __restrict__ partials;     // [gridDim.x][NPART]
+  unsigned* __restrict__ counter;
+  double* __restrict__ diag;         // [DIAG_CAP][NREC]
+  unsigned long long* __restrict__ diag_count;
+  double* __restrict__ clprof;       // [Nx]
+};
+
+struct RedSmem {
+  double col[4][TY][TX];
+  double wsum[TY][6];
+  double wmin[TY];
+  int wimin[TY];
+  int last;
+};
+
+// Warp-level FP64 sum and (min, argmin) with ties to the smaller column.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ void warp_min(double& v, int& idx) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov < v || (ov == v && oi < idx)) {
+      v = ov;
+      idx = oi;
+    }
+  }
+}
+
+// Column sums -> next step's density correction, C_l(x), per-CTA partials;
+// the last CTA to finish reduces the partials in CTA order into one record.
+__device__ __forceinline__ void column_epilogue(const Lat& L, const StepArgs& a, int x,
+                                                const double acc[4], RedSmem& rs) {
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * TX + tx;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) rs.col[k][ty][tx] = acc[k];
+  __syncthreads();
+  if (ty == 0) {
+    double c[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      double v = 0.0;
+      for (int t = 0; t < TY; ++t) v += rs.col[k][t][tx];
+      c[k] = v;
+    }
+    const bool in = interior(L, x);
+    if (x < L.Nx) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) a.cs_out[(size_t)k * L.Nx + x] = c[k];
+    }
+    double Cl = 0.0;
+    if (in) {
+      double na = c[0] * L.s[0], nb = c[1] * L.s[1];
+      Cl = (L.light == 0 ? na : nb) / (na + nb);
+      a.clprof[x] = Cl;
+    } else if (x < L.Nx) {
+      a.clprof[x] = (x == 0) ? L.C_in : L.C_out;
+    }
+    double vmin = in ? Cl : INFINITY;
+    int imin = in ? x : 0x7fffffff;
+    warp_min(vmin, imin);
+    double p_dev = warp_sum(in ? Cl - L.C_in : 0.0);
+    double p_ma = warp_sum(in ? c[2] : 0.0);
+    double p_mb = warp_sum(in ? c[3] : 0.0);
+    double p_ra = warp_sum(in ? c[0] : 0.0);
+    double p_rb = warp_sum(in ? c[1] : 0.0);
+    double p_n = warp_sum(in ? 1.0 : 0.0);
+    if (tx == 0) {
+      double* p = a.partials + (size_t)blockIdx.x * NPART;
+      p[0] = vmin;
+      p[1] = (double)imin;
+      p[2] = p_dev;
+      p[3] = p_ma;
+      p[4] = p_mb;
+      p[5] = p_ra;
+      p[6] = p_rb;
+      p[7] = p_n;
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned ticket = atomicAdd(a.counter, 1u);
+    rs.last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!rs.last) return;
+  __threadfence();
+  // Last CTA: every thread folds a fixed subset of the partials in CTA order,
+  // then a fixed shuffle tree per warp and warp order in thread 0, so the
+  // result does not depend on which CTA finished last.
+  const int nt = TX * TY;
+  double vmin = INFINITY, sm[6] = {0, 0, 0, 0, 0, 0};
+  int imin = 0x7fffffff;
+  for (int b = tid; b < (int)gridDim.x; b += nt) {
+    const double* p = a.partials + (size_t)b * NPART;
+    double v = __ldcg(p + 0);
+    int i = (int)__ldcg(p + 1);
+    if (v < vmin || (v == vmin && i < imin)) {
+      vmin = v;
+      imin = i;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sm[k] += __ldcg(p + 2 + k);
+  }
+  warp_min(vmin, imin);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) sm[k] = warp_sum(sm[k]);
+  const int lane = tid & 31, wid = tid >> 5;
+  if (lane == 0) {
+    rs.wmin[wid] = vmin;
+    rs.wimin[wid] = imin;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) rs.wsum[wid][k] = sm[k];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double tot[6] = {0, 0, 0, 0, 0, 0};
+    double mn = INFINITY;
+    int im = 0x7fffffff;
+    for (int w = 0; w < nt / 32; ++w) {
+      for (int k = 0; k < 6; ++k) tot[k] += rs.wsum[w][k];
+      if (rs.wmin[w] < mn || (rs.wmin[w] == mn && rs.wimin[w] < im)) {
+        mn = rs.wmin[w];
+        im = rs.wimin[w];
+      }
+    }
+    double dev = tot[0];
+    if (!L.x_periodic) dev += (L.C_out - L.C_in);  // the outlet boundary column
+    const double ncol = tot[5];
+    unsigned long long cnt = *a.diag_count + 1ull;
+    double* rec = a.diag + (size_t)((cnt - 1ull) % DIAG_CAP) * NREC;
+    rec[0] = (double)cnt;
+    rec[1] = (L.C_in - mn) / L.C_in;
+    rec[2] = dev / ((double)L.Nx * L.C_in);
+    rec[3] = tot[1] / ncol;
+    rec[4] = tot[2] / ncol;
+    rec[5] = (double)im;
+    rec[6] = tot[3];
+    rec[7] = tot[4];
+    *a.diag_count = cnt;
+    *a.counter = 0u;
+    __threadfence();
+  }
+}
+
+__global__ void __launch_bounds__(TX* TY) lbm_step_kernel(Lat L, StepArgs a) {
+  __shared__ WallSmem wsm;
+  __shared__ RedSmem rsm;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x = blockIdx.x * TX + tx;
+  const Ends E = load_ends(L, a.cs_in);
+  wall_prologue<true>(L, a.fin, a.alpha, E, x, wsm);
+  const bool in = interior(L, x);
+  const float r_bot = wsm.r[0][tx], r_top = wsm.r[1][tx];
+  const int half = (L.N + 1) / 2;  // rows j < half (1-based 2J <= N+1) use the bottom tau_q
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  if (in) {
+    for (int j = ty; j < L.N; j += TY) {
+      float fs[2][9];
+      pull_node(a.fin, L, E, x, j, r_bot, r_top, fs);
+      Macro m;
+      macro(L, fs, m);
+      float tau_s, tau_d;
+      taus(L, m, (float)j + 0.5f, tau_s, tau_d);
+      const float om_s = 1.0f / tau_s, om_d = 1.0f / tau_d;
+      const float om_q = wsm.om_q[j < half ? 0 : 1][tx];
+#pragma unroll
+      for (int sp = 0; sp < 2; ++sp) {
+        float mxs = collide(fs[sp], m.rho[sp], L.s[sp], m.ux, m.uy, L.om_e, L.om_eps, om_d,
+                            om_q, om_s);
+        acc[sp] += (double)m.rho[sp];
+        acc[2 + sp] += (double)mxs;
+        float* o = a.fout + sp * L.spec_stride + j * L.pitch + x;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) o[i * L.pop_stride] = fs[sp][i];
+      }
+    }
+  }
+  column_epilogue(L, a, x, acc, rsm);
+}
+
+// ---------------------------------------------------------- moments kernel
+// Fields of the state obtained by streaming fin (direct = 0), or of fin
+// itself (direct = 1), FP64 [6][N][Nx]: rho_a, rho_b, u_a (x, y), u_b (x, y)
+// with the species momentum of Eq. rhou.
+__global__ void __launch_bounds__(TX* TY) lbm_moments_kernel(Lat L, const float* __restrict__ fin,
+                                                              const double* __restrict__ cs_in,
+                                                              const float* __restrict__ alpha,
+                                                              int direct, double* __restrict__ out) {
+  __shared__ WallSmem wsm;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x = blockIdx.x * TX + tx;
+  const Ends E = load_ends(L, cs_in);
+  if (!direct) wall_prologue<false>(L, fin, alpha, E, x, wsm);
+  if (!interior(L, x)) return;
+  const size_t plane = (size_t)L.N * L.Nx;
+  for (int j = ty; j < L.N; j += TY) {
+    float fs[2][9];
+    if (direct) {
+#pragma unroll
+      for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fs[sp][i] = ld(fin, L, sp, i, j, x);
+    } else {
+      pull_node(fin, L, E, x, j, wsm.r[0][tx], wsm.r[1][tx], fs);
+    }
+    Macro m;
+    macro(L, fs, m);
+    float tau_s, tau_d;
+    taus(L, m, (float)j + 0.5f, tau_s, tau_d);
+    const float w1 = (2.0f * tau_d - 1.0f) / (2.0f * tau_d), w2 = 1.0f / (2.0f * tau_d);
+    const size_t o = (size_t)j * L.Nx + x;
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+      float mx = fmaf(w1, m.jx[sp], w2 * m.rho[sp] * m.ux);
+      float my = fmaf(w1, m.jy[sp], w2 * m.rho[sp] * m.uy);
+      out[sp * plane + o] = (double)m.rho[sp];
+      out[(2 + 2 * sp) * plane + o] = (double)(mx / m.rho[sp]);
+      out[(3 + 2 * sp) * plane + o] = (double)(my / m.rho[sp]);
+    }
+  }
+}
+
+// Boundary columns of the moment fields (pressure ends): rho_s =
+// kappa_s (2 rho_s(1) - rho_s(2)) with kappa_s of Eq. rho2, u_s linearly
+// extrapolated.  Block 0: inlet, block 1: outlet.
+__global__ void lbm_moments_ends_kernel(Lat L, double* __restrict__ out) {
+  __shared__ double red[2][256];
+  const int end = blockIdx.x, tid = threadIdx.x;
+  const int xb = end == 0 ? 0 : L.Nx - 1, x1 = end == 0 ? 1 : L.Nx - 2,
+            x2 = end == 0 ? 2 : L.Nx - 3;
+  const size_t plane = (size_t)L.N * L.Nx;
+  double sa = 0.0, sb = 0.0;
+  for (int j = tid; j < L.N; j += blockDim.x) {
+    size_t o = (size_t)j * L.Nx;
+    sa += 2.0 * out[o + x1] - out[o + x2];
+    sb += 2.0 * out[plane + o + x1] - out[plane + o + x2];
+  }
+  red[0][tid] = sa;
+  red[1][tid] = sb;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (tid < w) {
+      red[0][tid] += red[0][tid + w];
+      red[1][tid] += red[1][tid + w];
+    }
+    __syncthreads();
+  }
+  const double* tgt = end == 0 ? L.rho_in : L.rho_out;
+  const double ka = L.N * tgt[0] / red[0][0], kb = L.N * tgt[1] / red[1][0];
+  for (int j = tid; j < L.N; j += blockDim.x) {
+    size_t o = (size_t)j * L.Nx;
+    out[o + xb] = ka * (2.0 * out[o + x1] - out[o + x2]);
+    out[plane + o + xb] = kb * (2.0 * out[plane + o + x1] - out[plane + o + x2]);
+    for (int k = 2; k < 6; ++k)
+      out[k * plane + o + xb] = 2.0 * out[k * plane + o + x1] - out[k * plane + o + x2];
+  }
+}
+
+// ------------------------------------------------------------ init kernels
+// Equilibrium at rest (Eq. feq with u = 0: f_i = w_i alpha_si rho_s) of the
+// linear pressure / composition profile; periodic mode uses the outlet
+// state everywhere.
+__global__ void lbm_init_kernel(Lat L, float* __restrict__ f, double theta) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (x >= L.Nx || j >= L.N) return;
+  double t = L.x_periodic ? 1.0 : (double)x / (L.Nx - 1);
+  double n = L.x_periodic ? 1.0 : theta + (1.0 - theta) * t;
+  const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                       1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+  for (int sp = 0; sp < 2; ++sp) {
+    double Cl = L.C_in + (L.C_out - L.C_in) * t;
+    double C = (sp == L.light) ? Cl : 1.0 - Cl;
+    double s = (double)L.s[sp];
+    double rho = n * C * L.mh[sp];
+    for (int i = 0; i < 9; ++i) {
+      double al = i == 0 ? (9.0 - 5.0 * s) / 4.0 : s;
+      f[sp * L.spec_stride + i * L.pop_stride + j * L.pitch + x] = (float)(w[i] * al * rho);
+    }
+  }
+}
+
+// Column sums of a post-collision state (densities and raw x momenta), used
+// as the density-correction input of the first step after init or a state
+// upload.
+__global__ void lbm_colsum_kernel(Lat L, const float* __restrict__ f, double* __restrict__ cs) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= L.Nx) return;
+  for (int sp = 0; sp < 2; ++sp) {
+    double r = 0.0, m = 0.0;
+    for (int j = 0; j < L.N; ++j) {
+      float v[9];
+      for (int i = 0; i < 9; ++i) v[i] = ld(f, L, sp, i, j, x);
+      r += (double)(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8]);
+      m += (double)((v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]));
+    }
+    cs[(size_t)sp * L.Nx + x] = r;
+    cs[(size_t)(2 + sp) * L.Nx + x] = m;
+  }
+}
+
+// Steady-state residual over the column sums: R = |c - c_old| / (K |c|),
+// then c_old = c.  One CTA.
+__global__ void lbm_residual_kernel(const double* __restrict__ c, double* __restrict__ c_old,
+                                    long n, double K, int have_old, double* __restrict__ R) {
+  __shared__ double s1[32], s2[32];
+  double d2 = 0.0, c2 = 0.0;
+  for (long k = threadIdx.x; k < n; k += blockDim.x) {
+    double v = c[k];
+    double d = v - c_old[k];
+    d2 += d * d;
+    c2 += v * v;
+    c_old[k] = v;
+  }
+  d2 = warp_sum(d2);
+  c2 = warp_sum(c2);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    s1[wid] = d2;
+    s2[wid] = c2;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    d2 = lane < nw ? s1[lane] : 0.0;
+    c2 = lane < nw ? s2[lane] : 0.0;
+    d2 = warp_sum(d2);
+    c2 = warp_sum(c2);
+    if (lane == 0) *R = have_old ? sqrt(d2) / (K * sqrt(c2)) : INFINITY;
+  }
+}
+
+__global__ void lbm_special_kernel(const double* __restrict__ x, double* __restrict__ e1,
+                                   double* __restrict__ ps, long n) {
+  long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  float v = (float)x[k];
+  e1[k] = (double)e1_dev(v);
+  ps[k] = (double)psi_dev(v);
+}
+
+}  // namespace
+
+// ================================================================ host API
+struct lbm_mix {
+  lbm_mix_params p;
+  Lat L;
+  int device;
+  cudaStream_t stream;
+  bool own_stream;
+  int nblocks;
+  float* buf[2];
+  double* cs[2];
+  double* cs_snap;
+  float* alpha;
+  double* partials;
+  unsigned* counter;
+  double* diag;
+  unsigned long long* diag_count;
+  double* clprof;
+  double* resid;
+  double* mom;
+  double* h_pinned;  // small pinned staging area
+  int cur;           // buffer holding the latest post-collision state
+  long steps;
+  bool have_snap;
+};
+
+namespace {
+
+int validate(const lbm_mix_params* p, int* Nx_out) {
+  if (!p) return set_err(LBM_EINVAL, "params is NULL");
+  if (!(p->m_a > 0 && p->m_b > 0 && isfinite(p->m_a) && isfinite(p->m_b)))
+    return set_err(LBM_EINVAL, "masses must be positive and finite");
+  if (!(p->C_l > 0 && p->C_l < 1)) return set_err(LBM_EINVAL, "C_l must be in (0,1)");
+  if (p->C_l_out >= 0 && !(p->C_l_out > 0 && p->C_l_out < 1))
+    return set_err(LBM_EINVAL, "C_l_out must be in (0,1) or negative");
+  if (!(p->theta >= 1.0 && isfinite(p->theta))) return set_err(LBM_EINVAL, "theta must be >= 1");
+  if (!(p->Kn_out > 0 && isfinite(p->Kn_out))) return set_err(LBM_EINVAL, "Kn_out must be > 0");
+  if (p->N < 2) return set_err(LBM_EINVAL, "N must be >= 2");
+  long Nx = p->N_x;
+  if (Nx <= 0) {
+    if (!(p->L_over_H > 0 && isfinite(p->L_over_H)))
+      return set_err(LBM_EINVAL, "L_over_H must be > 0 when N_x <= 0");
+    Nx = lround(p->N * p->L_over_H);
+  }
+  if (Nx < 4) return set_err(LBM_EINVAL, "need N_x >= 4 columns (got %ld)", Nx);
+  if (!(p->accommodation > 0 && p->accommodation <= 1))
+    return set_err(LBM_EINVAL, "accommodation must be in (0,1]");
+  if (!(p->c_m0 >= 0 && isfinite(p->c_m0))) return set_err(LBM_EINVAL, "c_m0 must be >= 0");
+  if (!(p->tau_rho > 0.5 && p->tau_e > 0.5 && p->tau_eps > 0.5))
+    return set_err(LBM_EINVAL, "tau_rho, tau_e, tau_eps must exceed 1/2");
+  if (!(p->mu_ratio_a > 0 && p->mu_ratio_b > 0))
+    return set_err(LBM_EINVAL, "viscosity ratios must be > 0");
+  if (p->storage != LBM_FP32) return set_err(LBM_EINVAL, "storage must be LBM_FP32");
+  if (p->x_periodic != 0 && p->x_periodic != 1) return set_err(LBM_EINVAL, "x_periodic is 0 or 1");
+  long pitch = (Nx + 31) / 32 * 32;
+  double elems = 18.0 * (double)p->N * (double)pitch;
+  if (elems >= 2147483648.0)
+    return set_err(LBM_EINVAL, "lattice too large: 18*N*pitch must stay below 2^31");
+  *Nx_out = (int)Nx;
+  return LBM_OK;
+}
+
+// Lattice constants in the units of the header (k_B T = 1/3, m_min = 1,
+// outlet number density 1), derived in FP64.
+Lat derive(const lbm_mix_params* p, int Nx) {
+  Lat L;
+  memset(&L, 0, sizeof L);
+  const double PI = 3.14159265358979323846;
+  L.N = p->N;
+  L.Nx = Nx;
+  L.pitch = (Nx + 31) / 32 * 32;
+  L.pop_stride = (unsigned)((long)L.N * L.pitch);
+  L.spec_stride = 9u * L.pop_stride;
+  L.x_periodic = p->x_periodic;
+  double m_min = fmin(p->m_a, p->m_b);
+  double mh[2] = {p->m_a / m_min, p->m_b / m_min};
+  L.light = (p->m_a <= p->m_b) ? 0 : 1;
+  double Cin = p->C_l, Cout = p->C_l_out < 0 ? p->C_l : p->C_l_out;
+  double Ci[2], Co[2];
+  Ci[L.light] = Cin;
+  Ci[1 - L.light] = 1.0 - Cin;
+  Co[L.light] = Cout;
+  Co[1 - L.light] = 1.0 - Cout;
+  L.C_in = Cin;
+  L.C_out = Cout;
+  double mx_out = Co[0] * mh[0] + Co[1] * mh[1];
+  double lam_out = p->Kn_out * p->N;
+  // lambda = (mu / p) sqrt(pi k_B T / (2 m_x)) with p_out = 1/3 at the outlet
+  double mu = lam_out * (1.0 / 3.0) / sqrt(PI / (6.0 * mx_out));
+  double mu_s[2] = {p->mu_ratio_a * mu, p->mu_ratio_b * mu};
+  for (int sp = 0; sp < 2; ++sp) {
+    L.s[sp] = (float)(1.0 / mh[sp]);
+    L.mh[sp] = mh[sp];
+    double cxl = 3.0 * mu_s[sp] * sqrt(PI / (6.0 * mh[sp]));
+    L.c_xl[sp] = (float)cxl;
+    L.inv_c_xl[sp] = (float)(1.0 / cxl);
+    L.rho_in[sp] = p->theta * Ci[sp] * mh[sp];
+    L.rho_out[sp] = Co[sp] * mh[sp];
+  }
+  double clam = 3.0 * mu * sqrt(PI / 6.0);
+  L.c_lam = (float)clam;
+  L.inv_c_lam = (float)(1.0 / clam);
+  L.c_ts = (float)sqrt(6.0 / PI);
+  L.c_td = (float)(1.5 * sqrt(3.0 * (mh[0] + mh[1]) * mh[0] * mh[1] / 1.0));
+  L.om_e = (float)(1.0 / p->tau_e);
+  L.om_eps = (float)(1.0 / p->tau_eps);
+  L.c_m0 = (float)p->c_m0;
+  L.H = (float)p->N;
+  return L;
+}
+
+int launch_colsum(lbm_mix* h, int b) {
+  dim3 blk(128), grd((h->L.Nx + 127) / 128);
+  lbm_colsum_kernel<<<grd, blk, 0, h->stream>>>(h->L, h->buf[b], h->cs[b]);
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+int reset_diag(lbm_mix* h) {
+  CK(cudaMemsetAsync(h->diag_count, 0, sizeof(unsigned long long), h->stream));
+  CK(cudaMemsetAsync(h->diag, 0, sizeof(double) * DIAG_CAP * NREC, h->stream));
+  h->have_snap = false;
+  return LBM_OK;
+}
+
+int launch_step(lbm_mix* h) {
+  StepArgs a;
+  const int b = h->cur;
+  a.fin = h->buf[b];
+  a.fout = h->buf[1 - b];
+  a.cs_in = h->cs[b];
+  a.cs_out = h->cs[1 - b];
+  a.alpha = h->alpha;
+  a.partials = h->partials;
+  a.counter = h->counter;
+  a.diag = h->diag;
+  a.diag_count = h->diag_count;
+  a.clprof = h->clprof;
+  dim3 blk(TX, TY), grd(h->nblocks);
+  lbm_step_kernel<<<grd, blk, 0, h->stream>>>(h->L, a);
+  CK(cudaGetLastError());
+  h->cur = 1 - b;
+  h->steps++;
+  return LBM_OK;
+}
+
+int launch_moments(lbm_mix* h, double* d_out) {
+  // The state of step n is the stream of buffer P_{n-1}; right after init or
+  // an upload only the buffer itself exists.
+  const bool direct = (h->steps == 0);
+  const int b = direct ? h->cur : 1 - h->cur;
+  dim3 blk(TX, TY), grd(h->nblocks);
+  lbm_moments_kernel<<<grd, blk, 0, h->stream>>>(h->L, h->buf[b], h->cs[b], h->alpha,
+                                                 direct ? 1 : 0, d_out);
+  CK(cudaGetLastError());
+  if (!h->L.x_periodic) {
+    lbm_moments_ends_kernel<<<2, 256, 0, h->stream>>>(h->L, d_out);
+    CK(cudaGetLastError());
+  }
+  return LBM_OK;
+}
+
+int check_handle(const lbm_mix* h) {
+  if (!h) return set_err(LBM_EINVAL, "handle is NULL");
+  return LBM_OK;
+}
+
+// Latest diagnostic record (host copy). Returns LBM_ENONFINITE on NaN/Inf.
+int latest_record(lbm_mix* h, double rec[NREC]) {
+  unsigned long long cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, h->diag_count, sizeof cnt, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (cnt == 0) return set_err(LBM_EINVAL, "no step taken yet");
+  CK(cudaMemcpyAsync(rec, h->diag + ((cnt - 1) % DIAG_CAP) * NREC, sizeof(double) * NREC,
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int k = 1; k < NREC; ++k)
+    if (!isfinite(rec[k])) return set_err(LBM_ENONFINITE, "non-finite diagnostic at step %llu", cnt);
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_mix_default_params(lbm_mix_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof *p);
+  p->m_a = 4.003;
+  p->m_b = 39.948;
+  p->C_l = 0.5;
+  p->C_l_out = -1.0;
+  p->theta = 2.0;
+  p->Kn_out = 0.1;
+  p->N = 16;
+  p->N_x = 0;
+  p->L_over_H = 20.0;
+  p->accommodation = 1.0;
+  p->c_m0 = 1.016;
+  p->tau_rho = 1.0;
+  p->tau_e = 1.1;
+  p->tau_eps = 1.2;
+  p->mu_ratio_a = 1.0;
+  p->mu_ratio_b = 1.0;
+  p->storage = LBM_FP32;
+  p->x_periodic = 0;
+}
+
+const char* lbm_mix_strerror(int s) {
+  switch (s) {
+    case LBM_OK: return "success";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "out of memory";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_ENONFINITE: return "non-finite value in the state";
+    case LBM_ENOTCONVERGED: return "not converged within max_steps";
+    case LBM_ETIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+const char* lbm_mix_last_error(void) { return g_err; }
+
+void lbm_mix_destroy(lbm_mix* h) {
+  if (!h) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  cudaFree(h->buf[0]);
+  cudaFree(h->buf[1]);
+  cudaFree(h->cs[0]);
+  cudaFree(h->cs[1]);
+  cudaFree(h->cs_snap);
+  cudaFree(h->alpha);
+  cudaFree(h->partials);
+  cudaFree(h->counter);
+  cudaFree(h->diag);
+  cudaFree(h->diag_count);
+  cudaFree(h->clprof);
+  cudaFree(h->resid);
+  cudaFree(h->mom);
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  cudaSetDevice(prev);
+  delete h;
+}
+
+int lbm_mix_create(const lbm_mix_params* p, void* stream, lbm_mix** out) {
+  if (!out) return set_err(LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  int Nx = 0;
+  int st = validate(p, &Nx);
+  if (st != LBM_OK) return st;
+  lbm_mix* h = new (std::nothrow) lbm_mix;
+  if (!h) return set_err(LBM_ENOMEM, "host allocation failed");
+  memset(h, 0, sizeof *h);
+  h->p = *p;
+  h->L = derive(p, Nx);
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return set_err(LBM_ECUDA, "no CUDA device");
+  }
+  h->nblocks = (Nx + TX - 1) / TX;
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return set_err(LBM_ECUDA, "cudaStreamCreate failed");
+    }
+    h->own_stream = true;
+  }
+  const size_t fbytes = sizeof(float) * 18 * (size_t)h->L.N * h->L.pitch;
+  const size_t cbytes = sizeof(double) * 4 * (size_t)Nx;
+  cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, bytes) \
+  if (e == cudaSuccess) e = cudaMalloc((void**)&(ptr), (bytes))
+  ALLOC(h->buf[0], fbytes);
+  ALLOC(h->buf[1], fbytes);
+  ALLOC(h->cs[0], cbytes);
+  ALLOC(h->cs[1], cbytes);
+  ALLOC(h->cs_snap, cbytes);
+  ALLOC(h->alpha, sizeof(float) * 2 * (size_t)Nx);
+  ALLOC(h->partials, sizeof(double) * NPART * (size_t)h->nblocks);
+  ALLOC(h->counter, sizeof(unsigned));
+  ALLOC(h->diag, sizeof(double) * DIAG_CAP * NREC);
+  ALLOC(h->diag_count, sizeof(unsigned long long));
+  ALLOC(h->clprof, sizeof(double) * (size_t)Nx);
+  ALLOC(h->resid, sizeof(double));
+#undef ALLOC
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_pinned, sizeof(double) * 64);
+  if (e != cudaSuccess) {
+    int code = (e == cudaErrorMemoryAllocation) ? LBM_ENOMEM : LBM_ECUDA;
+    set_err(code, "allocation failed: %s", cudaGetErrorString(e));
+    cudaGetLastError();
+    lbm_mix_destroy(h);
+    return code;
+  }
+  // zero everything so that padding and ghost columns hold defined values
+  e = cudaMemsetAsync(h->buf[0], 0, fbytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, fbytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->counter, 0, sizeof(unsigned), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->cs[0], 0, cbytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->cs[1], 0, cbytes, h->stream);
+  if (e == cudaSuccess) {
+    float* a = (float*)malloc(sizeof(float) * 2 * Nx);
+    if (!a) e = cudaErrorMemoryAllocation;
+    else {
+      for (int k = 0; k < 2 * Nx; ++k) a[k] = (float)p->accommodation;
+      e = cudaMemcpyAsync(h->alpha, a, sizeof(float) * 2 * Nx, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      free(a);
+    }
+  }
+  if (e != cudaSuccess) {
+    set_err(LBM_ECUDA, "initialisation failed: %s", cudaGetErrorString(e));
+    lbm_mix_destroy(h);
+    return LBM_ECUDA;
+  }
+  if (reset_diag(h) != LBM_OK) {
+    lbm_mix_destroy(h);
+    return LBM_ECUDA;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_mix_init(lbm_mix* h) {
+  int st = check_handle(h);
+  if (st) return st;
+  h->cur = 0;
+  h->steps = 0;
+  dim3 blk(128), grd((h->L.Nx + 127) / 128, h->L.N);
+  lbm_init_kernel<<<grd, blk, 0, h->stream>>>(h->L, h->buf[0], h->p.theta);
+  CK(cudaGetLastError());
+  if ((st = launch_colsum(h, 0))) return st;
+  return reset_diag(h);
+}
+
+int lbm_mix_step(lbm_mix* h, long nsteps) {
+  int st = check_handle(h);
+  if (st) return st;
+  if (nsteps < 0) return set_err(LBM_EINVAL, "nsteps < 0");
+  for (long t = 0; t < nsteps; ++t)
+    if ((st = launch_step(h))) return st;
+  return LBM_OK;
+}
+
+int lbm_mix_run_to_steady(lbm_mix* h, double tol, long max_steps, long check_every,
+                          long* steps_out, double* residual_out) {
+  int st = check_handle(h);
+  if (st) return st;
+  if (!(tol > 0) || max_steps < 0 || check_every < 1)
+    return set_err(LBM_EINVAL, "need tol > 0, max_steps >= 0, check_every >= 1");
+  long taken = 0;
+  double R = INFINITY;
+  const long n = 4L * h->L.Nx;
+  int result = LBM_ENOTCONVERGED;
+  while (taken < max_steps) {
+    long k = check_every < max_steps - taken ? check_every : max_steps - taken;
+    if ((st = lbm_mix_step(h, k))) return st;
+    taken += k;
+    lbm_residual_kernel<<<1, 1024, 0, h->stream>>>(h->cs[h->cur], h->cs_snap, n, (double)k,
+                                                   h->have_snap ? 1 : 0, h->resid);
+    CK(cudaGetLastError());
+    h->have_snap = true;
+    CK(cudaMemcpyAsync(h->h_pinned, h->resid, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    R = h->h_pinned[0];
+    if (isnan(R)) {
+      result = set_err(LBM_ENONFINITE, "non-finite residual after %ld steps", taken);
+      break;
+    }
+    if (R <= tol) {
+      result = LBM_OK;
+      break;
+    }
+  }
+  if (steps_out) *steps_out = taken;
+  if (residual_out) *residual_out = R;
+  if (result == LBM_ENOTCONVERGED)
+    set_err(LBM_ENOTCONVERGED, "residual %.3e above %.3e after %ld steps", R, tol, taken);
+  return result;
+}
+
+int lbm_mix_moments_device(lbm_mix* h, double* d_out) {
+  int st = check_handle(h);
+  if (st) return st;
+  if (!d_out) return set_err(LBM_EINVAL, "d_out is NULL");
+  return launch_moments(h, d_out);
+}
+
+int lbm_mix_moments(lbm_mix* h, double* rho_a, double* rho_b, double* ua_x, double* ua_y,
+                    double* ub_x, double* ub_y) {
+  int st = check_handle(h);
+  if (st) return st;
+  const size_t plane = (size_t)h->L.N * h->L.Nx;
+  if (!h->mom) CK(cudaMalloc((void**)&h->mom, sizeof(double) * 6 * plane));
+  if ((st = launch_moments(h, h->mom))) return st;
+  double* outs[6] = {rho_a, rho_b, ua_x, ua_y, ub_x, ub_y};
+  for (int k = 0; k < 6; ++k)
+    if (outs[k])
+      CK(cudaMemcpyAsync(outs[k], h->mom + k * plane, sizeof(double) * plane,
+                         cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_mix_separation(lbm_mix* h, double* CL, double* Cl_tilde, double* mdot_a, double* mdot_b,
+                       double* Cl_profile, int* x_min) {
+  int st = check_handle(h);
+  if (st) return st;
+  double rec[NREC];
+  if ((st = latest_record(h, rec))) return st;
+  if (CL) *CL = rec[1];
+  if (Cl_tilde) *Cl_tilde = rec[2];
+  if (mdot_a) *mdot_a = rec[3];
+  if (mdot_b) *mdot_b = rec[4];
+  if (x_min) *x_min = (int)rec[5];
+  if (Cl_profile) {
+    CK(cudaMemcpyAsync(Cl_profile, h->clprof, sizeof(double) * h->L.Nx, cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return LBM_OK;
+}
+
+int lbm_mix_history(lbm_mix* h, double* rec, long max_records, long* count) {
+  int st = check_handle(h);
+  if (st) return st;
+  if (!rec || max_records < 0 || !count) return set_err(LBM_EINVAL, "bad history arguments");
+  unsigned long long cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, h->diag_count, sizeof cnt, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  long have = (long)(cnt < (unsigned long long)DIAG_CAP ? cnt : DIAG_CAP);
+  long take = have < max_records ? have : max_records;
+  for (long k = 0; k < take; ++k) {
+    unsigned long long idx = (cnt - take + k) % DIAG_CAP;
+    CK(cudaMemcpyAsync(rec + k * NREC, h->diag + idx * NREC, sizeof(double) * NREC,
+                       cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  *count = take;
+  return LBM_OK;
+}
+
+int lbm_mix_set_accommodation_field(lbm_mix* h, const double* alpha, long n) {
+  int st = check_handle(h);
+  if (st) return st;
+  if (!alpha || n != 2L * h->L.Nx) return set_err(LBM_EINVAL, "need 2*N_x accommodation values");
+  float* a = (float*)malloc(sizeof(float) * n);
+  if (!a) return set_err(LBM_ENOMEM, "host allocation failed");
+  for (long k = 0; k < n; ++k) {
+    if (!(alpha[k] > 0 && alpha[k] <= 1)) {
+      free(a);
+      return set_err(LBM_EINVAL, "accommodation[%ld] = %g outside (0,1]", k, alpha[k]);
+    }
+    a[k] = (float)alpha[k];
+  }
+  cudaError_t e = cudaMemcpyAsync(h->alpha, a, sizeof(float) * n, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  free(a);
+  if (e != cudaSuccess) return set_err(LBM_ECUDA, "upload failed: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int lbm_mix_set_post_state(lbm_mix* h, const float* f, long n) {
+  int st = check_handle(h);
+  if (st) return st;
+  const long need = 18L * h->L.N * h->L.Nx;
+  if (!f || n != need) return set_err(LBM_EINVAL, "need %ld populations", need);
+  h->cur = 0;
+  h->steps = 0;
+  CK(cudaMemcpy2DAsync(h->buf[0], sizeof(float) * h->L.pitch, f, sizeof(float) * h->L.Nx,
+                       sizeof(float) * h->L.Nx, 18 * (size_t)h->L.N, cudaMemcpyHostToDevice,
+                       h->stream));
+  if ((st = launch_colsum(h, 0))) return st;
+  if ((st = reset_diag(h))) return st;
+  CK(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_mix_get_post_state(lbm_mix* h, float* f, long n) {
+  int st = check_handle(h);
+  if (st) return st;
+  const long need = 18L * h->L.N * h->L.Nx;
+  if (!f || n != need) return set_err(LBM_EINVAL, "need %ld populations", need);
+  CK(cudaMemcpy2DAsync(f, sizeof(float) * h->L.Nx, h->buf[h->cur], sizeof(float) * h->L.pitch,
+                       sizeof(float) * h->L.Nx, 18 * (size_t)h->L.N, cudaMemcpyDeviceToHost,
+                       h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_mix_dims(const lbm_mix* h, int* N, int* N_x, long* steps) {
+  int st = check_handle(h);
+  if (st) return st;
+  if (N) *N = h->L.N;
+  if (N_x) *N_x = h->L.Nx;
+  if (steps) *steps = h->steps;
+  return LBM_OK;
+}
+
+int lbm_mix_sync(lbm_mix* h) {
+  int st = check_handle(h);
+  if (st) return st;
+  CK(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_mix_eval_special(const double* x, double* e1, double* psi, long n) {
+  if (!x || n < 0) return set_err(LBM_EINVAL, "bad arguments");
+  if (n == 0) return LBM_OK;
+  for (long k = 0; k < n; ++k)
+    if (!(x[k] > 0)) return set_err(LBM_EINVAL, "x[%ld] must be > 0", k);
+  double *dx = nullptr, *de = nullptr, *dp = nullptr;
+  const size_t b = sizeof(double) * n;
+  cudaError_t e = cudaMalloc((void**)&dx, b);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&de, b);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dp, b);
+  if (e == cudaSuccess) e = cudaMemcpy(dx, x, b, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    lbm_special_kernel<<<(unsigned)((n + 255) / 256), 256>>>(dx, de, dp, n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && e1) e = cudaMemcpy(e1, de, b, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && psi) e = cudaMemcpy(psi, dp, b, cudaMemcpyDeviceToHost);
+  cudaFree(dx);
+  cudaFree(de);
+  cudaFree(dp);
+  if (e != cudaSuccess) return set_err(LBM_ECUDA, "eval_special: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,240 @@
+"""GPU parity: the sm_103a fused step (through the C ABI) against the FP64
+oracle, element by element, on the same seeded inputs.
+
+Tolerances (FP32 storage and arithmetic against FP64): densities to 1e-5 of
+their maximum, species velocities to RTOL_U of their maximum, scalar
+diagnostics as stated per test.  See the tolerance derivation in the design
+notes: one FP32 rounding of a population is ~6e-8 of the density; the
+velocity is a difference of populations ~30x smaller than the density, and
+errors accumulate over the relaxation time of the channel.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1603_08221_gb300 import binding, workloads
+
+pytestmark = pytest.mark.gpu
+
+RTOL_RHO = 1e-5
+RTOL_U = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _libs():
+    binding.load()
+    oracle.build()
+
+
+def _relerr(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _pair(params, steps, post_state=None, alpha=None):
+    g = binding.LbmMix(**params)
+    o = oracle.Oracle(params)
+    if post_state is None:
+        g.init()
+        o.init()
+    else:
+        g.set_post_state(post_state.astype(np.float32))
+        o.set_post_state(post_state.astype(np.float32).astype(np.float64))
+    if alpha is not None:
+        g.set_accommodation_field(alpha)
+        o.set_accommodation_field(alpha)
+    g.step(steps)
+    o.step(steps)
+    return g, o
+
+
+def _check_moments(g, o, rtol_rho=RTOL_RHO, rtol_u=RTOL_U):
+    mg, mo = g.moments(), o.moments()
+    for k in ("rho_a", "rho_b"):
+        assert np.isfinite(mg[k]).all()
+        assert _relerr(mg[k], mo[k]) < rtol_rho, (k, _relerr(mg[k], mo[k]))
+    for k in ("ua_x", "ua_y", "ub_x", "ub_y"):
+        scale = max(np.abs(mo["ua_x"]).max(), np.abs(mo["ub_x"]).max(), 1e-12)
+        err = np.abs(mg[k] - mo[k]).max() / scale
+        assert err < rtol_u, (k, err)
+    return mg, mo
+
+
+# ------------------------------------------------------ special functions
+def test_device_E1_and_psi():
+    x = np.concatenate([np.geomspace(1e-5, 0.999, 60), [1.0], np.geomspace(1.001, 80, 80)])
+    e1, ps = binding.lbm_mix_eval_special(x)
+    ref_e1 = np.array([oracle.E1(v) for v in x])
+    ref_ps = np.array([oracle.psi(v) for v in x])
+    assert np.abs(e1 / ref_e1 - 1).max() < 2e-6
+    assert np.abs(ps - ref_ps).max() < 1e-6
+
+
+# --------------------------------------------------------------- stepping
+@pytest.mark.parametrize("N,Nx", [(4, 6), (8, 8), (2, 5)])
+@pytest.mark.parametrize("steps", [1, 100])
+def test_tiny_grids(N, Nx, steps):
+    p = workloads.preset("heli_argon_320x16", N=N, N_x=Nx)
+    g, o = _pair(p, steps)
+    _check_moments(g, o)
+    fp_g = g.get_post_state()[:, :, :, 1:-1]
+    fp_o = o.get_post_state()[:, :, :, 1:-1]
+    assert _relerr(fp_g, fp_o) < RTOL_RHO
+
+
+def test_ragged_multi_tile_channel():
+    """Several 32-column strips with a ragged last strip (100 columns) and a
+    row count that is not a multiple of the 8-row sweep (20 rows)."""
+    p = workloads.preset("neon_argon_2048x32", N=20, N_x=100)
+    g, o = _pair(p, 300)
+    _check_moments(g, o)
+    sg, so = g.separation(), o.separation()
+    assert abs(sg["CL"] - so["CL"]) < 1e-6 + 1e-3 * abs(so["CL"])
+    assert abs(sg["Cl_tilde"] - so["Cl_tilde"]) < 1e-6 + 1e-3 * abs(so["Cl_tilde"])
+    assert abs(sg["mdot_a"] / so["mdot_a"] - 1) < RTOL_U
+    assert abs(sg["mdot_b"] / so["mdot_b"] - 1) < RTOL_U
+    assert np.abs(sg["Cl_profile"] - so["Cl_profile"]).max() < 1e-6
+
+
+def test_unequal_end_composition_and_accommodation_field():
+    p = workloads.preset("heli_argon_320x16", N=10, N_x=40, C_l_out=0.3)
+    alpha = workloads.random_accommodation(40, seed=1, spread=0.3)
+    g, o = _pair(p, 200, alpha=alpha)
+    _check_moments(g, o)
+
+
+def test_random_state_periodic_channel():
+    p = workloads.preset("heli_argon_320x16", N=8, N_x=40, x_periodic=1)
+    f0 = workloads.random_post_state(8, 40, seed=3, lo=0.09, hi=0.11)
+    g, o = _pair(p, 40, post_state=f0)
+    _check_moments(g, o, rtol_u=1e-3)
+
+
+def test_mass_conservation_fp32():
+    """Periodic in x between DBB walls: total species masses stay constant
+    to FP32 round-off over 2000 steps (per-step records, FP64 sums)."""
+    p = workloads.preset("heli_argon_320x16", N=16, N_x=64, x_periodic=1)
+    g = binding.LbmMix(**p)
+    g.set_post_state(workloads.random_post_state(16, 64, seed=5, lo=0.09, hi=0.11))
+    g.step(2000)
+    h = g.history(4096)
+    assert len(h) == 2000 and h[-1, 0] == 2000
+    ma, mb = h[:, 6], h[:, 7]
+    assert np.abs(ma / ma[0] - 1).max() < 2e-6
+    assert np.abs(mb / mb[0] - 1).max() < 2e-6
+
+
+def test_rest_state_fixed_point():
+    p = workloads.preset("heli_argon_320x16", N=8, N_x=30, theta=1.0)
+    g = binding.LbmMix(**p)
+    g.init()
+    f0 = g.get_post_state()
+    g.step(500)
+    f1 = g.get_post_state()
+    assert np.abs(f1 - f0)[:, :, :, 1:-1].max() < 1e-6 * np.abs(f0).max()
+
+
+def test_identical_species_no_separation():
+    p = dict(m_a=1.0, m_b=1.0, C_l=0.3, theta=2.0, Kn_out=0.2, N=12, N_x=60)
+    g = binding.LbmMix(**p)
+    g.init()
+    g.step(400)
+    f = g.get_post_state()[:, :, :, 1:-1]
+    assert np.abs(f[0] / f[1] - 0.3 / 0.7).max() < 1e-5
+    s = g.separation()
+    assert abs(s["CL"]) < 1e-6 and abs(s["Cl_tilde"]) < 1e-6
+
+
+def test_history_matches_oracle_separation():
+    p = workloads.preset("heli_argon_320x16", N=8, N_x=48)
+    g = binding.LbmMix(**p)
+    o = oracle.Oracle(p)
+    g.init()
+    o.init()
+    cl = []
+    for _ in range(5):
+        g.step(60)
+        o.step(60)
+        cl.append(o.separation()["CL"])
+    h = g.history()
+    assert len(h) == 300
+    assert list(h[59::60, 0]) == [60, 120, 180, 240, 300]
+    got = h[59::60, 1]
+    assert np.abs(got - np.array(cl)).max() < 1e-6 + 1e-3 * np.abs(cl).max()
+
+
+def test_moments_device_matches_host():
+    torch = pytest.importorskip("torch")
+    p = workloads.preset("heli_argon_320x16", N=8, N_x=40)
+    stream = torch.cuda.Stream()
+    g = binding.LbmMix(stream=stream, **p)
+    g.init()
+    g.step(20)
+    out = torch.empty((6, 8, 40), dtype=torch.float64, device="cuda")
+    binding.lbm_mix_moments_device(g.h, out.data_ptr())
+    g.sync()
+    host = g.moments()
+    dev = out.cpu().numpy()
+    for k, name in enumerate(["rho_a", "rho_b", "ua_x", "ua_y", "ub_x", "ub_y"]):
+        assert np.array_equal(dev[k], host[name])
+
+
+def test_post_state_roundtrip_and_errors():
+    p = workloads.preset("heli_argon_320x16", N=6, N_x=20)
+    g = binding.LbmMix(**p)
+    f = workloads.random_post_state(6, 20, seed=9).astype(np.float32)
+    g.set_post_state(f)
+    assert np.array_equal(g.get_post_state(), f)
+    with pytest.raises(binding.LbmError):
+        g.set_accommodation_field(np.full(40, 1.5))
+    with pytest.raises(binding.LbmError):
+        g.set_post_state(f[:, :, :, :10])
+    with pytest.raises(binding.LbmError):
+        binding.lbm_mix_separation(g.h)  # no step yet
+
+
+def test_run_to_steady():
+    p = workloads.preset("heli_argon_320x16", N=8, N_x=24, theta=1.5, Kn_out=0.2)
+    g = binding.LbmMix(**p)
+    g.init()
+    st, steps, R = g.run_to_steady(1e-7, 20000, 100)
+    assert st == binding.LBM_OK and R <= 1e-7 and steps < 20000
+    st, steps, R = g.run_to_steady(1e-30, 300, 100)
+    assert st == binding.LBM_ENOTCONVERGED and steps == 300
+
+
+# ------------------------------------------------------- named workloads
+def test_helium_argon_320x16_20000_steps():
+    """He-Ar, C_l = 0.5, theta = 2, Kn_out = 0.1, 320 x 16, 20 000 steps:
+    GPU FP32 against the FP64 oracle on rho_s, u_s, mdot_s and CL."""
+    p = workloads.preset("heli_argon_320x16")
+    g, o = _pair(p, 20000)
+    _check_moments(g, o)
+    sg, so = g.separation(), o.separation()
+    assert abs(sg["CL"] / so["CL"] - 1) < 1e-3, (sg["CL"], so["CL"])
+    assert abs(sg["mdot_a"] / so["mdot_a"] - 1) < RTOL_U
+    assert abs(sg["mdot_b"] / so["mdot_b"] - 1) < RTOL_U
+    assert sg["x_min"] == so["x_min"]
+
+
+def test_neon_argon_full_size_one_step():
+    """The 32768 x 512 throughput workload in the launch configuration the
+    benchmark times: after 3 GPU steps, the oracle takes the GPU's
+    post-collision state and advances it one step; every node's moments of
+    that step must match the GPU's."""
+    p = workloads.preset("neon_argon_32768x512")
+    g = binding.LbmMix(**p)
+    g.init()
+    g.step(3)
+    fp = g.get_post_state()
+    g.step(1)
+    mg = g.moments()
+    o = oracle.Oracle(p)
+    o.set_post_state(fp.astype(np.float64))
+    del fp
+    o.step(1)
+    mo = o.moments()
+    for k in ("rho_a", "rho_b"):
+        assert _relerr(mg[k], mo[k]) < RTOL_RHO, k
+    scale = max(np.abs(mo["ua_x"]).max(), np.abs(mo["ub_x"]).max())
+    for k in ("ua_x", "ua_y", "ub_x", "ub_y"):
+        assert np.abs(mg[k] - mo[k]).max() / scale < RTOL_U, k
