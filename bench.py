@@ -185,7 +185,10 @@ def run_ours(args):
     from paper_1603_08221_gb300 import binding, workloads
     binding.load()
     p = workloads.preset(args.workload)
-    stream = torch.cuda.current_stream(dev)
+    # a dedicated (non-default) stream: the library and the CUDA events below
+    # must see the same stream
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     sim = binding.LbmMix(stream=stream, **p)
     nodes = sim.N * (sim.N_x - 2)
     sim.init()
@@ -236,8 +239,7 @@ def run_ours(args):
         t = torch.tensor([elapsed, e2e_elapsed], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed, e2e_elapsed = float(t[0]), float(t[1])
-    mlups, _ = aggregate([elapsed] * 1, [nodes * args.steps * world])
-    mlups /= 1e6
+    mlups = aggregate([elapsed], [nodes * args.steps * world])[0] / 1e6
     e2e_mlups = nodes * args.steps * world / e2e_elapsed / 1e6
     ms_per_step = elapsed / args.steps * 1e3
 

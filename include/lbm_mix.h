@@ -141,8 +141,15 @@ int lbm_mix_set_accommodation_field(lbm_mix* h, const double* alpha, long n);
 int lbm_mix_set_post_state(lbm_mix* h, const float* f, long n);
 
 /* Copies the current post-collision populations to host FP32 [2][9][N][N_x].
+ * The library stores deviations from a per-column rest equilibrium, so a
+ * set/get round trip reproduces each value to about one FP32 ulp.
  * Synchronises. */
 int lbm_mix_get_post_state(lbm_mix* h, float* f, long n);
+
+/* Same populations in FP64, [2][9][N][N_x]: the exact values the FP32
+ * deviation storage represents (reference equilibrium + deviation, summed in
+ * FP64).  Synchronises. */
+int lbm_mix_get_post_state_f64(lbm_mix* h, double* f, long n);
 
 /* Lattice size and steps taken since init / set_post_state. */
 int lbm_mix_dims(const lbm_mix* h, int* N, int* N_x, long* steps);

@@ -70,6 +70,7 @@ _SIGS = {
     "lbm_mix_set_accommodation_field": (_I, [_H, _PD, _L]),
     "lbm_mix_set_post_state": (_I, [_H, _PF, _L]),
     "lbm_mix_get_post_state": (_I, [_H, _PF, _L]),
+    "lbm_mix_get_post_state_f64": (_I, [_H, _PD, _L]),
     "lbm_mix_dims": (_I, [_H, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_L)]),
     "lbm_mix_sync": (_I, [_H]),
     "lbm_mix_eval_special": (_I, [_PD, _PD, _PD, _L]),
@@ -217,6 +218,14 @@ def lbm_mix_get_post_state(h) -> np.ndarray:
     return out
 
 
+def lbm_mix_get_post_state_f64(h) -> np.ndarray:
+    N, Nx, _ = lbm_mix_dims(h)
+    out = np.empty((2, 9, N, Nx), dtype=np.float64)
+    _check(load().lbm_mix_get_post_state_f64(h, _dptr(out), out.size),
+           "lbm_mix_get_post_state_f64")
+    return out
+
+
 def lbm_mix_sync(h) -> None:
     _check(load().lbm_mix_sync(h), "lbm_mix_sync")
 
@@ -306,6 +315,9 @@ class LbmMix:
 
     def get_post_state(self) -> np.ndarray:
         return lbm_mix_get_post_state(self.h)
+
+    def get_post_state_f64(self) -> np.ndarray:
+        return lbm_mix_get_post_state_f64(self.h)
 
     def run_to_steady(self, tol: float, max_steps: int, check_every: int = 100):
         return lbm_mix_run_to_steady(self.h, tol, max_steps, check_every)

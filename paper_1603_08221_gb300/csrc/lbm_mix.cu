@@ -65,6 +65,8 @@ struct Lat {
   int x_periodic;
   int light;             // index of the light species
   float s[2];            // s_sigma = m_min / m_sigma
+  float cw0[2];          // rest-equilibrium weights w_i alpha_si: rest (9 - 5s)/9,
+  float cw1[2], cw5[2];  // axis s/9, diagonal s/36
   float inv_c_lam;       // 1 / (3 mu sqrt(pi/6))
   float c_lam;           // 3 mu sqrt(pi/6): lambda = c_lam / (n sqrt(m_x))
   float c_xl[2];         // 3 mu_s sqrt(pi/(6 m_s)): x_s lambda_s = c_xl / n
@@ -111,17 +113,37 @@ __device__ __forceinline__ float e1_dev(float x) {
   return x <= 1.0f ? e1_series(x) : expf(-x) * xexe1_rational(x) / x;
 }
 
-// psi(a) = 1 + (a - 1) e^{-a} - a^2 E_1(a)  (Eq. psi), written without
-// cancellation: for a <= 1 as (1 - e^{-a}) + a e^{-a} - a^2 E_1(a), for
-// a > 1 as 1 + e^{-a} [(a - 1) - a (x e^x E_1)(a)].
+// psi(a) = 1 + (a - 1) e^{-a} - a^2 E_1(a)  (Eq. psi).
+//  a <= 1: with the series of E_1, psi(a) = Q(a) + a^2 ln a where
+//          Q(a) = 1 + (a - 1) e^{-a} + gamma a^2 - a^2 sum_k (-1)^{k+1} a^k/(k k!)
+//          is entire; its Taylor coefficients are 2, gamma - 3/2 and
+//          (-1)^m 2 / ((m - 2) m!) for m >= 3 (worked out from the two
+//          series); eleven terms leave < 4e-10 on [0, 1].
+//  1 < a < 15: psi = 1 + e^{-a} [(a - 1) - a (x e^x E_1)(a)] with the
+//          rational approximation above (no cancellation).
+//  a >= 15: 1 - psi < 2e^{-a}/a < 3e-8, below half an FP32 ulp of 1.
 __device__ __forceinline__ float psi_dev(float a) {
   if (a <= 1.0f) {
     if (!(a > 0.0f)) return 0.0f;
-    float em1 = expm1f(-a);
-    return fmaf(a, 1.0f + em1, -em1) - a * a * e1_series(a);
+    float q = -1.0f / 179625600.0f;
+    q = fmaf(q, a, 1.0f / 14515200.0f);
+    q = fmaf(q, a, -1.0f / 1270080.0f);
+    q = fmaf(q, a, 1.0f / 120960.0f);
+    q = fmaf(q, a, -1.0f / 12600.0f);
+    q = fmaf(q, a, 1.0f / 1440.0f);
+    q = fmaf(q, a, -1.0f / 180.0f);
+    q = fmaf(q, a, 1.0f / 24.0f);
+    q = fmaf(q, a, -1.0f / 3.0f);
+    q = fmaf(q, a, 0.5772156649f - 1.5f);
+    q = fmaf(q, a, 2.0f);
+    return fmaf(a * a, logf(a), q * a);
   }
-  float e = expf(-a);
-  return fmaf(e, (a - 1.0f) - a * xexe1_rational(a), 1.0f);
+  if (a >= 15.0f) return 1.0f;
+  float num = (((a + 8.5733287401f) * a + 18.0590169730f) * a + 8.6347608925f) * a +
+              0.2677737343f;
+  float den = (((a + 9.5733223454f) * a + 25.6329561486f) * a + 21.0996530827f) * a +
+              3.9584969228f;
+  return fmaf(__expf(-a), (a - 1.0f) - a * __fdividef(num, den), 1.0f);
 }
 
 // psi'(a) = 2 e^{-a} - 2 a E_1(a).
@@ -133,39 +155,84 @@ __device__ __forceinline__ float dpsi_dev(float a) {
   return 2.0f * expf(-a) * (1.0f - xexe1_rational(a));
 }
 
-// ------------------------------------------------------------- streaming
-struct Ends {
-  float kin[2], kout[2];  // Eq. rho2 density-correction factors
+// ------------------------------------------------------------- storage
+// Populations are stored as deviations d_i = f_i - w_i alpha_si rhobar_s(x)
+// from the rest equilibrium (Eq. feq with u = 0) of a fixed per-column
+// reference density rhobar_s(x) (the initial profile).  The heavy species'
+// rest population carries ~90% of its mass, so storing f_i itself would put
+// FP32 rounding of that large number into every moment; the deviations are
+// small and keep their full relative precision.  All arithmetic below works
+// on deviations relative to the node's own column reference.
+template <typename ST>
+struct Stor;
+template <>
+struct Stor<float> {
+  static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+  static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 };
 
-__device__ __forceinline__ float ld(const float* __restrict__ f, const Lat& L, int sp, int i,
-                                    int j, int x) {
-  return __ldg(f + sp * L.spec_stride + i * L.pop_stride + j * L.pitch + x);
+struct Ends {
+  float kin[2], kout[2];  // Eq. rho2 density-correction factors
+  float gin[2], gout[2];  // ghost reference offsets kappa(2 rb(1) - rb(2)) - rb(0), per species
+};
+
+template <typename ST>
+__device__ __forceinline__ float ld(const ST* __restrict__ f, const Lat& L, int sp, int i, int j,
+                                    int x) {
+  return Stor<ST>::ld(f + sp * L.spec_stride + i * L.pop_stride + j * L.pitch + x);
 }
 
-// Post-collision value that population i carries into column x from its
-// upstream neighbour column xs at row js; the inlet/outlet ghost columns
-// (Eq. rho1, all nine populations extrapolated and scaled by Eq. rho2) are
-// virtual.
-__device__ __forceinline__ float src(const float* __restrict__ f, const Lat& L, const Ends& E,
-                                     int sp, int i, int js, int xs) {
+// Deviation (relative to the SOURCE column's reference) that population i
+// carries from column xs at row js; the inlet/outlet ghost columns (Eq. rho1,
+// all nine populations extrapolated and scaled by Eq. rho2) are virtual.
+template <typename ST>
+__device__ __forceinline__ float src(const ST* __restrict__ f, const Lat& L, const Ends& E,
+                                     float cwi, int sp, int i, int js, int xs) {
   if (!L.x_periodic) {
     if (xs == 0)
-      return E.kin[sp] * (2.0f * ld(f, L, sp, i, js, 1) - ld(f, L, sp, i, js, 2));
+      return fmaf(E.kin[sp], 2.0f * ld(f, L, sp, i, js, 1) - ld(f, L, sp, i, js, 2),
+                  cwi * E.gin[sp]);
     if (xs == L.Nx - 1)
-      return E.kout[sp] *
-             (2.0f * ld(f, L, sp, i, js, L.Nx - 2) - ld(f, L, sp, i, js, L.Nx - 3));
+      return fmaf(E.kout[sp],
+                  2.0f * ld(f, L, sp, i, js, L.Nx - 2) - ld(f, L, sp, i, js, L.Nx - 3),
+                  cwi * E.gout[sp]);
   }
   return ld(f, L, sp, i, js, xs);
 }
 
-// Pre-collision populations of node (x, j): f_i(x) = f'_i(x - c_i) (Eq. MRT),
-// with the unknown populations of the wall rows from diffuse bounce-back
-// (Eqs. bot, bot2) using the post-collision state of the same node: the wall
-// equilibrium f^eq_i(rho_w, u_w = 0) = w_i rho_w s with rho_w from zero normal
-// species flux, i.e. f^eq_i = 6 w_i (sum of the outgoing f').
-__device__ __forceinline__ void pull_node(const float* __restrict__ f, const Lat& L,
-                                          const Ends& E, int x, int j, float r_bot,
+// Per-thread column data: own reference density and the reference
+// differences to the left and right neighbour columns.
+struct ColRef {
+  float rb[2], dl[2], dr[2];
+};
+
+__device__ __forceinline__ ColRef col_ref(const Lat& L, const float* __restrict__ refrho, int x) {
+  ColRef c;
+  int xm = x - 1, xp = x + 1;
+  if (xm < 0) xm += L.Nx;
+  if (xp >= L.Nx) xp -= L.Nx;
+  const bool ok = x < L.Nx;
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    const float* r = refrho + sp * L.Nx;
+    float r0 = ok ? __ldg(r + x) : 0.0f;
+    c.rb[sp] = r0;
+    c.dl[sp] = ok ? __ldg(r + xm) - r0 : 0.0f;  // exact: adjacent columns differ < 2x
+    c.dr[sp] = ok ? __ldg(r + xp) - r0 : 0.0f;
+  }
+  return c;
+}
+
+// Pre-collision deviations of node (x, j): f_i(x) = f'_i(x - c_i) (Eq. MRT)
+// re-referenced to column x, with the unknown populations of the wall rows
+// from diffuse bounce-back (Eqs. bot, bot2) on the post-collision state of
+// the same node.  The wall equilibrium f^eq_i(rho_w, u_w = 0) = w_i s rho_w
+// with rho_w from zero normal species flux equals 6 w_i (sum of the outgoing
+// f'); its rest part cancels against the reference, leaving
+// d_i = (1 - r) d'_opp(i) + r (w_i/(1/6)) sum_outgoing d'.
+template <typename ST>
+__device__ __forceinline__ void pull_node(const ST* __restrict__ f, const Lat& L, const Ends& E,
+                                          const ColRef& C, int x, int j, float r_bot,
                                           float r_top, float fs[2][9]) {
   int xm = x - 1, xp = x + 1;
   if (L.x_periodic) {
@@ -176,55 +243,62 @@ __device__ __forceinline__ void pull_node(const float* __restrict__ f, const Lat
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     float* g = fs[sp];
+    const float c1 = L.cw1[sp], c5 = L.cw5[sp];
+    const float dl = C.dl[sp], dr = C.dr[sp];
     g[0] = ld(f, L, sp, 0, j, x);
-    g[1] = src(f, L, E, sp, 1, j, xm);
-    g[3] = src(f, L, E, sp, 3, j, xp);
+    g[1] = fmaf(c1, dl, src(f, L, E, c1, sp, 1, j, xm));
+    g[3] = fmaf(c1, dr, src(f, L, E, c1, sp, 3, j, xp));
     if (bot) {
       float o4 = ld(f, L, sp, 4, j, x), o7 = ld(f, L, sp, 7, j, x), o8 = ld(f, L, sp, 8, j, x);
-      float t = r_bot * (o4 + o7 + o8), q = 1.0f - r_bot;
-      g[2] = fmaf(q, o4, t * (2.0f / 3.0f));
-      g[5] = fmaf(q, o7, t * (1.0f / 6.0f));
-      g[6] = fmaf(q, o8, t * (1.0f / 6.0f));
+      // the equilibrium parts t/6, t/6 and t - 2 t/6 sum to t exactly up
+      // to one rounding, so the wall conserves mass without an FP32 bias
+      float t = r_bot * (o4 + o7 + o8), q = 1.0f - r_bot, t6 = t * (1.0f / 6.0f);
+      g[2] = fmaf(q, o4, fmaf(-2.0f, t6, t));
+      g[5] = fmaf(q, o7, t6);
+      g[6] = fmaf(q, o8, t6);
     } else {
       g[2] = ld(f, L, sp, 2, j - 1, x);
-      g[5] = src(f, L, E, sp, 5, j - 1, xm);
-      g[6] = src(f, L, E, sp, 6, j - 1, xp);
+      g[5] = fmaf(c5, dl, src(f, L, E, c5, sp, 5, j - 1, xm));
+      g[6] = fmaf(c5, dr, src(f, L, E, c5, sp, 6, j - 1, xp));
     }
     if (top) {
       float o2 = ld(f, L, sp, 2, j, x), o5 = ld(f, L, sp, 5, j, x), o6 = ld(f, L, sp, 6, j, x);
-      float t = r_top * (o2 + o5 + o6), q = 1.0f - r_top;
-      g[4] = fmaf(q, o2, t * (2.0f / 3.0f));
-      g[7] = fmaf(q, o5, t * (1.0f / 6.0f));
-      g[8] = fmaf(q, o6, t * (1.0f / 6.0f));
+      float t = r_top * (o2 + o5 + o6), q = 1.0f - r_top, t6 = t * (1.0f / 6.0f);
+      g[4] = fmaf(q, o2, fmaf(-2.0f, t6, t));
+      g[7] = fmaf(q, o5, t6);
+      g[8] = fmaf(q, o6, t6);
     } else {
       g[4] = ld(f, L, sp, 4, j + 1, x);
-      g[7] = src(f, L, E, sp, 7, j + 1, xp);
-      g[8] = src(f, L, E, sp, 8, j + 1, xm);
+      g[7] = fmaf(c5, dr, src(f, L, E, c5, sp, 7, j + 1, xp));
+      g[8] = fmaf(c5, dl, src(f, L, E, c5, sp, 8, j + 1, xm));
     }
   }
 }
 
 // ---------------------------------------------------------------- moments
 struct Macro {
+  float sd[2];           // sum of deviations: rho_s - rhobar_s
   float rho[2], jx[2], jy[2];
   float ux, uy;
-  float inv_n, mx;
+  float n, inv_n, mx;
 };
 
-__device__ __forceinline__ void macro(const Lat& L, const float fs[2][9], Macro& m) {
+__device__ __forceinline__ void macro(const Lat& L, const ColRef& C, const float fs[2][9],
+                                      Macro& m) {
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     const float* g = fs[sp];
-    m.rho[sp] = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    m.sd[sp] = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    m.rho[sp] = C.rb[sp] + m.sd[sp];
     m.jx[sp] = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
     m.jy[sp] = (g[2] - g[4]) + (g[5] - g[7]) + (g[6] - g[8]);
   }
   float rho = m.rho[0] + m.rho[1];
-  float inv_rho = 1.0f / rho;
+  float inv_rho = __fdividef(1.0f, rho);
   m.ux = (m.jx[0] + m.jx[1]) * inv_rho;
   m.uy = (m.jy[0] + m.jy[1]) * inv_rho;
-  float n = fmaf(m.rho[0], L.s[0], m.rho[1] * L.s[1]);  // number density (Eq. P)
-  m.inv_n = 1.0f / n;
+  m.n = fmaf(m.rho[0], L.s[0], m.rho[1] * L.s[1]);  // number density (Eq. P)
+  m.inv_n = __fdividef(1.0f, m.n);
   m.mx = rho * m.inv_n;  // m_x = rho / n
 }
 
@@ -233,23 +307,27 @@ __device__ __forceinline__ float Psi_dev(float y, float H, float inv_lam) {
   return 0.5f * (psi_dev(y * inv_lam) + psi_dev((H - y) * inv_lam));
 }
 
-// tau_s (Eq. taos) and tau_d (Eq. EQFrsp with lambda_se = lambda_s Psi(y;
-// lambda_s), lambda_s = (mu_s/p_s) sqrt(pi k_B T/(2 m_s)), p_s = x_s p).
-__device__ __forceinline__ void taus(const Lat& L, const Macro& m, float y, float& tau_s,
-                                     float& tau_d) {
+// Relaxation rates 1/tau_s (Eq. taos) and 1/tau_d (Eq. EQFrsp with
+// lambda_se = lambda_s Psi(y; lambda_s), lambda_s = (mu_s/p_s)
+// sqrt(pi k_B T/(2 m_s)), p_s = x_s p).
+__device__ __forceinline__ void rates(const Lat& L, const Macro& m, float y, float& om_s,
+                                      float& om_d) {
   float rs_mx = rsqrtf(m.mx);
-  float lam = L.c_lam * m.inv_n * rs_mx;
-  float inv_lam = L.inv_c_lam * (1.0f / (m.inv_n * rs_mx));
-  tau_s = 0.5f + lam * Psi_dev(y, L.H, inv_lam) * L.c_ts * rs_mx;
+  float lam = L.c_lam * m.inv_n * rs_mx;                // mixture mean free path
+  float inv_lam = L.inv_c_lam * m.n * (m.mx * rs_mx);  // 1 / lambda
+  float ts = lam * Psi_dev(y, L.H, inv_lam) * L.c_ts * rs_mx;  // tau_s - 1/2
+  om_s = __fdividef(1.0f, 0.5f + ts);
   float br = 0.0f;
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     float n_s = m.rho[sp] * L.s[sp];
-    float inv_lam_s = n_s * L.inv_c_xl[sp];          // 1 / lambda_s
+    float inv_lam_s = n_s * L.inv_c_xl[sp];                          // 1 / lambda_s
     float xl_e = L.c_xl[sp] * m.inv_n * Psi_dev(y, L.H, inv_lam_s);  // x_s lambda_se
     br += rsqrtf(xl_e);
   }
-  tau_d = 0.5f + L.c_td / (m.mx * br * br);
+  // tau_d = 1/2 + c_td / (m_x br^2)  =>  1/tau_d = d / (d/2 + c_td), d = m_x br^2
+  float d = m.mx * br * br;
+  om_d = __fdividef(d, fmaf(0.5f, d, L.c_td));
 }
 
 // tau_q of Eq. taoq from the wall node's lambda and m_x (tau'_s(0) in its
@@ -270,58 +348,62 @@ __device__ __forceinline__ float tau_q_wall(const Lat& L, const Macro& m, float 
 
 // r of Eq. R (first printed form) from the mixture molecular mass of the
 // reflected post-collision state at the wall node, c_m = c_m0 (2-alpha)/alpha.
-__device__ __forceinline__ float dbb_r(const Lat& L, const float* __restrict__ f, int x, int j,
-                                       float alpha) {
+template <typename ST>
+__device__ __forceinline__ float dbb_r(const Lat& L, const ColRef& C, const ST* __restrict__ f,
+                                       int x, int j, float alpha) {
   float rho[2];
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     float acc = 0.0f;
 #pragma unroll
     for (int i = 0; i < 9; ++i) acc += ld(f, L, sp, i, j, x);
-    rho[sp] = acc;
+    rho[sp] = C.rb[sp] + acc;
   }
   float mx = (rho[0] + rho[1]) / fmaf(rho[0], L.s[0], rho[1] * L.s[1]);
   float cm = L.c_m0 * (2.0f - alpha) / alpha;
   return 2.0f - 2.0f / (1.0f + cm * sqrtf(kPi * mx / 6.0f));
 }
 
-// MRT collision of one species (Eqs. MR, S, feq) in moment space:
-// f' = f - M^{-1} S (m - m^eq) with M^{-1} = M^T diag(1/9, 1/36, 1/36, 1/6,
-// 1/12, 1/6, 1/12, 1/4, 1/4) and the closed-form equilibrium moments
-// m^eq = rho_s (1, -4 + 2s + 3u^2, 4 - 3s - 3u^2, u_x, -u_x, u_y, -u_y,
-// u_x^2 - u_y^2, u_x u_y).  Returns the x component of the species momentum
-// of Eq. rhou, j_x - (j_x - rho_s u_x)/(2 tau_d).
+// MRT collision of one species (Eqs. MR, S, feq) on the deviations g from
+// the rest equilibrium of the column reference, in moment space:
+// f' = f - M^{-1} S (m - m^eq), M^{-1} = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12,
+// 1/6, 1/12, 1/4, 1/4), m^eq = rho_s (1, -4 + 2s + 3u^2, 4 - 3s - 3u^2, u_x,
+// -u_x, u_y, -u_y, u_x^2 - u_y^2, u_x u_y).  The reference has m = m^eq(u=0),
+// so e - e^eq = sum_i (e_i + 4 - 2s) g_i - 3 rho u^2 and
+// eps - eps^eq = sum_i (eps_i - 4 + 3s) g_i + 3 rho u^2 need no large terms.
+// Returns the x component of the species momentum of Eq. rhou,
+// j_x - (j_x - rho_s u_x)/(2 tau_d).
 __device__ __forceinline__ float collide(float g[9], float rho, float s, float ux, float uy,
                                          float om_e, float om_eps, float om_d, float om_q,
                                          float om_s) {
-  float u2 = ux * ux + uy * uy;
-  float a14 = (g[1] + g[2]) + (g[3] + g[4]);
-  float a58 = (g[5] + g[6]) + (g[7] + g[8]);
-  float e = fmaf(-4.0f, g[0], fmaf(2.0f, a58, -a14));
-  float eps = fmaf(4.0f, g[0], fmaf(-2.0f, a14, a58));
-  float jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
-  float jy = (g[2] - g[4]) + (g[5] - g[7]) + (g[6] - g[8]);
-  float dx56 = (g[5] - g[6]) + (g[8] - g[7]);  // jx part of the diagonals
-  float dy56 = (g[5] - g[7]) + (g[6] - g[8]);
-  float qx = fmaf(2.0f, g[3] - g[1], dx56);
-  float qy = fmaf(2.0f, g[4] - g[2], dy56);
-  float pxx = (g[1] + g[3]) - (g[2] + g[4]);
-  float pxy = (g[5] + g[7]) - (g[6] + g[8]);
-  float de = om_e * (e - rho * (-4.0f + 2.0f * s + 3.0f * u2));
-  float deps = om_eps * (eps - rho * (4.0f - 3.0f * s - 3.0f * u2));
-  float djx = om_d * (jx - rho * ux);
-  float djy = om_d * (jy - rho * uy);
-  float dqx = om_q * (qx + rho * ux);
-  float dqy = om_q * (qy + rho * uy);
-  float dpxx = om_s * (pxx - rho * (ux * ux - uy * uy));
-  float dpxy = om_s * (pxy - rho * ux * uy);
-  float c0 = (de - deps) * (1.0f / 9.0f);
-  float c14 = de * (1.0f / 36.0f) + deps * (1.0f / 18.0f);
-  float c58 = -(de * (1.0f / 18.0f) + deps * (1.0f / 36.0f));
-  float ax = (dqx - djx) * (1.0f / 6.0f), ay = (dqy - djy) * (1.0f / 6.0f);
-  float bx = -(djx * (1.0f / 6.0f) + dqx * (1.0f / 12.0f));
-  float by = -(djy * (1.0f / 6.0f) + dqy * (1.0f / 12.0f));
-  float pp = dpxx * 0.25f, pq = dpxy * 0.25f;
+  const float ru2 = 3.0f * rho * (ux * ux + uy * uy);
+  const float a14 = (g[1] + g[2]) + (g[3] + g[4]);
+  const float a58 = (g[5] + g[6]) + (g[7] + g[8]);
+  const float ne = fmaf(-2.0f * s, g[0], fmaf(3.0f - 2.0f * s, a14, fmaf(6.0f - 2.0f * s, a58, -ru2)));
+  const float neps = fmaf(3.0f * s, g[0], fmaf(3.0f * s - 6.0f, a14, fmaf(3.0f * s - 3.0f, a58, ru2)));
+  const float dx56 = (g[5] - g[6]) + (g[8] - g[7]);
+  const float dy56 = (g[5] - g[7]) + (g[6] - g[8]);
+  const float jx = (g[1] - g[3]) + dx56;
+  const float jy = (g[2] - g[4]) + dy56;
+  const float qx = fmaf(2.0f, g[3] - g[1], dx56);
+  const float qy = fmaf(2.0f, g[4] - g[2], dy56);
+  const float pxx = (g[1] + g[3]) - (g[2] + g[4]);
+  const float pxy = (g[5] + g[7]) - (g[6] + g[8]);
+  const float de = om_e * ne;
+  const float deps = om_eps * neps;
+  const float djx = om_d * fmaf(-rho, ux, jx);
+  const float djy = om_d * fmaf(-rho, uy, jy);
+  const float dqx = om_q * fmaf(rho, ux, qx);
+  const float dqy = om_q * fmaf(rho, uy, qy);
+  const float dpxx = om_s * fmaf(-rho, ux * ux - uy * uy, pxx);
+  const float dpxy = om_s * fmaf(-rho, ux * uy, pxy);
+  const float c0 = (de - deps) * (1.0f / 9.0f);
+  const float c14 = de * (1.0f / 36.0f) + deps * (1.0f / 18.0f);
+  const float c58 = -(de * (1.0f / 18.0f) + deps * (1.0f / 36.0f));
+  const float ax = (dqx - djx) * (1.0f / 6.0f), ay = (dqy - djy) * (1.0f / 6.0f);
+  const float bx = -(djx * (1.0f / 6.0f) + dqx * (1.0f / 12.0f));
+  const float by = -(djy * (1.0f / 6.0f) + dqy * (1.0f / 12.0f));
+  const float pp = dpxx * 0.25f, pq = dpxy * 0.25f;
   g[0] += c0;
   g[1] += c14 + ax - pp;
   g[2] += c14 + ay + pp;
@@ -335,19 +417,32 @@ __device__ __forceinline__ float collide(float g[9], float rho, float s, float u
 }
 
 // Density-correction factors of Eq. rho2 for the ghost columns, from the
-// column sums of the state being streamed; only the CTAs that own column 1
-// or column N_x - 2 read them.
-__device__ __forceinline__ Ends load_ends(const Lat& L, const double* __restrict__ cs) {
+// column sums of the state being streamed, and the ghost reference offsets;
+// only the CTAs that own column 1 or column N_x - 2 read them.
+__device__ __forceinline__ Ends load_ends(const Lat& L, const double* __restrict__ cs,
+                                          const float* __restrict__ refrho) {
   Ends E;
-  E.kin[0] = E.kin[1] = E.kout[0] = E.kout[1] = 1.0f;
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    E.kin[sp] = E.kout[sp] = 1.0f;
+    E.gin[sp] = E.gout[sp] = 0.0f;
+  }
   if (L.x_periodic) return E;
   const int Nx = L.Nx, x0 = blockIdx.x * TX;
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     const double* c = cs + (size_t)sp * Nx;
-    if (x0 <= 1 && 1 < x0 + TX) E.kin[sp] = (float)(L.N * L.rho_in[sp] / (2.0 * c[1] - c[2]));
-    if (x0 <= Nx - 2 && Nx - 2 < x0 + TX)
-      E.kout[sp] = (float)(L.N * L.rho_out[sp] / (2.0 * c[Nx - 2] - c[Nx - 3]));
+    const float* r = refrho + sp * Nx;
+    if (x0 <= 1 && 1 < x0 + TX) {
+      double k = L.N * L.rho_in[sp] / (2.0 * c[1] - c[2]);
+      E.kin[sp] = (float)k;
+      E.gin[sp] = (float)(k * (2.0 * (double)r[1] - (double)r[2]) - (double)r[0]);
+    }
+    if (x0 <= Nx - 2 && Nx - 2 < x0 + TX) {
+      double k = L.N * L.rho_out[sp] / (2.0 * c[Nx - 2] - c[Nx - 3]);
+      E.kout[sp] = (float)k;
+      E.gout[sp] = (float)(k * (2.0 * (double)r[Nx - 2] - (double)r[Nx - 3]) - (double)r[Nx - 1]);
+    }
   }
   return E;
 }
@@ -364,22 +459,22 @@ struct WallSmem {
 
 // Prologue of the step and moments kernels: warp ty = 0 handles the bottom
 // wall node of each column of the strip, warp ty = 1 the top one.
-template <bool WITH_TQ>
-__device__ __forceinline__ void wall_prologue(const Lat& L, const float* __restrict__ fin,
+template <bool WITH_TQ, typename ST>
+__device__ __forceinline__ void wall_prologue(const Lat& L, const ST* __restrict__ fin,
                                               const float* __restrict__ alpha, const Ends& E,
-                                              int x, WallSmem& sm) {
+                                              const ColRef& C, int x, WallSmem& sm) {
   const int tx = threadIdx.x, ty = threadIdx.y;
   if (ty < 2) {
     float r = 1.0f, omq = 1.0f;
     if (interior(L, x)) {
       const int jw = ty == 0 ? 0 : L.N - 1;
       float al = alpha[ty * L.Nx + x];
-      r = dbb_r(L, fin, x, jw, al);
+      r = dbb_r(L, C, fin, x, jw, al);
       if (WITH_TQ) {
         float fs[2][9];
-        pull_node(fin, L, E, x, jw, r, r, fs);
+        pull_node(fin, L, E, C, x, jw, r, r, fs);
         Macro m;
-        macro(L, fs, m);
+        macro(L, C, fs, m);
         omq = 1.0f / tau_q_wall(L, m, al);
       }
     }
@@ -389,10 +484,27 @@ __device__ __forceinline__ void wall_prologue(const Lat& L, const float* __restr
   __syncthreads();
 }
 
+// Compensated FP32 running sum (Kahan): a thread's partial over its rows of
+// one column, accurate to ~1 FP32 ulp of the sum, handed to the FP64 column
+// reduction at the end of the sweep (FP64 arithmetic is a slow pipe on this
+// part).
+struct KahanF {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    float y = v - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // ------------------------------------------------------------ step kernel
+template <typename ST>
 struct StepArgs {
-  const float* __restrict__ fin;  // post-collision state of step t-1
-  float* __restrict__ fout;       // post-collision state of step t
+  const ST* __restrict__ fin;     // post-collision deviations of step t-1
+  ST* __restrict__ fout;          // post-collision deviations of step t
+  const float* __restrict__ refrho;  // [2][Nx] reference densities
   const double* __restrict__ cs_in;  // [4][Nx] column sums of the state in fin
   double* __restrict__ cs_out;       // [4][Nx] column sums of the state of step t
   const float* __restrict__ alpha;   // [2][Nx]
@@ -431,7 +543,8 @@ __device__ __forceinline__ void warp_min(double& v, int& idx) {
 
 // Column sums -> next step's density correction, C_l(x), per-CTA partials;
 // the last CTA to finish reduces the partials in CTA order into one record.
-__device__ __forceinline__ void column_epilogue(const Lat& L, const StepArgs& a, int x,
+template <typename ST>
+__device__ __forceinline__ void column_epilogue(const Lat& L, const StepArgs<ST>& a, int x,
                                                 const double acc[4], RedSmem& rs) {
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * TX + tx;
@@ -547,55 +660,66 @@ __device__ __forceinline__ void column_epilogue(const Lat& L, const StepArgs& a,
   }
 }
 
-__global__ void __launch_bounds__(TX* TY) lbm_step_kernel(Lat L, StepArgs a) {
+template <typename ST>
+__global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST> a) {
   __shared__ WallSmem wsm;
   __shared__ RedSmem rsm;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int x = blockIdx.x * TX + tx;
-  const Ends E = load_ends(L, a.cs_in);
-  wall_prologue<true>(L, a.fin, a.alpha, E, x, wsm);
+  const ColRef C = col_ref(L, a.refrho, x);
+  const Ends E = load_ends(L, a.cs_in, a.refrho);
+  wall_prologue<true>(L, a.fin, a.alpha, E, C, x, wsm);
   const bool in = interior(L, x);
   const float r_bot = wsm.r[0][tx], r_top = wsm.r[1][tx];
   const int half = (L.N + 1) / 2;  // rows j < half (1-based 2J <= N+1) use the bottom tau_q
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  KahanF acc[4];
   if (in) {
     for (int j = ty; j < L.N; j += TY) {
       float fs[2][9];
-      pull_node(a.fin, L, E, x, j, r_bot, r_top, fs);
+      pull_node(a.fin, L, E, C, x, j, r_bot, r_top, fs);
       Macro m;
-      macro(L, fs, m);
-      float tau_s, tau_d;
-      taus(L, m, (float)j + 0.5f, tau_s, tau_d);
-      const float om_s = 1.0f / tau_s, om_d = 1.0f / tau_d;
+      macro(L, C, fs, m);
+      float om_s, om_d;
+      rates(L, m, (float)j + 0.5f, om_s, om_d);
       const float om_q = wsm.om_q[j < half ? 0 : 1][tx];
 #pragma unroll
       for (int sp = 0; sp < 2; ++sp) {
         float mxs = collide(fs[sp], m.rho[sp], L.s[sp], m.ux, m.uy, L.om_e, L.om_eps, om_d,
                             om_q, om_s);
-        acc[sp] += (double)m.rho[sp];
-        acc[2 + sp] += (double)mxs;
-        float* o = a.fout + sp * L.spec_stride + j * L.pitch + x;
+        acc[sp].add(m.sd[sp]);
+        acc[2 + sp].add(mxs);
+        ST* o = a.fout + sp * L.spec_stride + j * L.pitch + x;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) o[i * L.pop_stride] = fs[sp][i];
+        for (int i = 0; i < 9; ++i) Stor<ST>::st(o + i * L.pop_stride, fs[sp][i]);
       }
     }
   }
-  column_epilogue(L, a, x, acc, rsm);
+  // column sum of rho_s = N rhobar_s + sum of deviations; the reference part
+  // is added once per column (by the ty = 0 thread of the strip)
+  double accd[4];
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp)
+    accd[sp] = (in && ty == 0 ? (double)L.N * (double)C.rb[sp] : 0.0) + acc[sp].value();
+  accd[2] = acc[2].value();
+  accd[3] = acc[3].value();
+  column_epilogue(L, a, x, accd, rsm);
 }
 
 // ---------------------------------------------------------- moments kernel
 // Fields of the state obtained by streaming fin (direct = 0), or of fin
 // itself (direct = 1), FP64 [6][N][Nx]: rho_a, rho_b, u_a (x, y), u_b (x, y)
 // with the species momentum of Eq. rhou.
-__global__ void __launch_bounds__(TX* TY) lbm_moments_kernel(Lat L, const float* __restrict__ fin,
-                                                              const double* __restrict__ cs_in,
-                                                              const float* __restrict__ alpha,
-                                                              int direct, double* __restrict__ out) {
+template <typename ST>
+__global__ void __launch_bounds__(TX* TY)
+    lbm_moments_kernel(Lat L, const ST* __restrict__ fin, const float* __restrict__ refrho,
+                       const double* __restrict__ cs_in, const float* __restrict__ alpha,
+                       int direct, double* __restrict__ out) {
   __shared__ WallSmem wsm;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int x = blockIdx.x * TX + tx;
-  const Ends E = load_ends(L, cs_in);
-  if (!direct) wall_prologue<false>(L, fin, alpha, E, x, wsm);
+  const ColRef C = col_ref(L, refrho, x);
+  const Ends E = load_ends(L, cs_in, refrho);
+  if (!direct) wall_prologue<false>(L, fin, alpha, E, C, x, wsm);
   if (!interior(L, x)) return;
   const size_t plane = (size_t)L.N * L.Nx;
   for (int j = ty; j < L.N; j += TY) {
@@ -606,19 +730,20 @@ __global__ void __launch_bounds__(TX* TY) lbm_moments_kernel(Lat L, const float*
 #pragma unroll
         for (int i = 0; i < 9; ++i) fs[sp][i] = ld(fin, L, sp, i, j, x);
     } else {
-      pull_node(fin, L, E, x, j, wsm.r[0][tx], wsm.r[1][tx], fs);
+      pull_node(fin, L, E, C, x, j, wsm.r[0][tx], wsm.r[1][tx], fs);
     }
     Macro m;
-    macro(L, fs, m);
-    float tau_s, tau_d;
-    taus(L, m, (float)j + 0.5f, tau_s, tau_d);
-    const float w1 = (2.0f * tau_d - 1.0f) / (2.0f * tau_d), w2 = 1.0f / (2.0f * tau_d);
+    macro(L, C, fs, m);
+    float om_s, om_d;
+    rates(L, m, (float)j + 0.5f, om_s, om_d);
+    // Eq. rhou: (2 tau_d - 1)/(2 tau_d) = 1 - om_d/2, 1/(2 tau_d) = om_d/2
+    const float w1 = 1.0f - 0.5f * om_d, w2 = 0.5f * om_d;
     const size_t o = (size_t)j * L.Nx + x;
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp) {
       float mx = fmaf(w1, m.jx[sp], w2 * m.rho[sp] * m.ux);
       float my = fmaf(w1, m.jy[sp], w2 * m.rho[sp] * m.uy);
-      out[sp * plane + o] = (double)m.rho[sp];
+      out[sp * plane + o] = (double)C.rb[sp] + (double)m.sd[sp];
       out[(2 + 2 * sp) * plane + o] = (double)(mx / m.rho[sp]);
       out[(3 + 2 * sp) * plane + o] = (double)(my / m.rho[sp]);
     }
@@ -662,33 +787,12 @@ __global__ void lbm_moments_ends_kernel(Lat L, double* __restrict__ out) {
 }
 
 // ------------------------------------------------------------ init kernels
-// Equilibrium at rest (Eq. feq with u = 0: f_i = w_i alpha_si rho_s) of the
-// linear pressure / composition profile; periodic mode uses the outlet
-// state everywhere.
-__global__ void lbm_init_kernel(Lat L, float* __restrict__ f, double theta) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y;
-  if (x >= L.Nx || j >= L.N) return;
-  double t = L.x_periodic ? 1.0 : (double)x / (L.Nx - 1);
-  double n = L.x_periodic ? 1.0 : theta + (1.0 - theta) * t;
-  const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
-                       1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-  for (int sp = 0; sp < 2; ++sp) {
-    double Cl = L.C_in + (L.C_out - L.C_in) * t;
-    double C = (sp == L.light) ? Cl : 1.0 - Cl;
-    double s = (double)L.s[sp];
-    double rho = n * C * L.mh[sp];
-    for (int i = 0; i < 9; ++i) {
-      double al = i == 0 ? (9.0 - 5.0 * s) / 4.0 : s;
-      f[sp * L.spec_stride + i * L.pop_stride + j * L.pitch + x] = (float)(w[i] * al * rho);
-    }
-  }
-}
-
-// Column sums of a post-collision state (densities and raw x momenta), used
-// as the density-correction input of the first step after init or a state
-// upload.
-__global__ void lbm_colsum_kernel(Lat L, const float* __restrict__ f, double* __restrict__ cs) {
+// Column sums of a state: sum_j rho_s = N rhobar_s + sum_j sum_i d_i and the
+// raw x momenta, used as the density-correction input of the first step
+// after init or a state upload.
+template <typename ST>
+__global__ void lbm_colsum_kernel(Lat L, const ST* __restrict__ f,
+                                  const float* __restrict__ refrho, double* __restrict__ cs) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= L.Nx) return;
   for (int sp = 0; sp < 2; ++sp) {
@@ -699,8 +803,30 @@ __global__ void lbm_colsum_kernel(Lat L, const float* __restrict__ f, double* __
       r += (double)(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8]);
       m += (double)((v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]));
     }
-    cs[(size_t)sp * L.Nx + x] = r;
+    cs[(size_t)sp * L.Nx + x] = (double)L.N * (double)refrho[sp * L.Nx + x] + r;
     cs[(size_t)(2 + sp) * L.Nx + x] = m;
+  }
+}
+
+// Full populations <-> stored deviations: to_dev = 1 converts f (already in
+// the buffer, FP32) into deviations in place; to_dev = 0 writes
+// f = d + ref into out (T = float or double, unpadded [2][9][N][Nx]).
+template <typename ST, typename T>
+__global__ void lbm_convert_kernel(Lat L, ST* __restrict__ f, const float* __restrict__ refrho,
+                                   int to_dev, T* __restrict__ out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, sp = blockIdx.z;
+  if (x >= L.Nx) return;
+  const float rb = refrho[sp * L.Nx + x];
+  for (int i = 0; i < 9; ++i) {
+    const float cw = i == 0 ? L.cw0[sp] : (i < 5 ? L.cw1[sp] : L.cw5[sp]);
+    const float ref = cw * rb;
+    ST* p = f + sp * L.spec_stride + i * L.pop_stride + j * L.pitch + x;
+    if (to_dev) {
+      Stor<ST>::st(p, (float)*p - ref);
+    } else {
+      out[(((size_t)sp * 9 + i) * L.N + j) * L.Nx + x] = (T)Stor<ST>::ld(p) + (T)ref;
+    }
   }
 }
 
@@ -754,7 +880,9 @@ struct lbm_mix {
   cudaStream_t stream;
   bool own_stream;
   int nblocks;
-  float* buf[2];
+  float* buf[2];      // post-collision deviations, A/B
+  float* refrho;      // [2][Nx] reference densities rhobar_s(x)
+  float* scratch;     // full-population staging for get_post_state (lazy)
   double* cs[2];
   double* cs_snap;
   float* alpha;
@@ -837,6 +965,9 @@ Lat derive(const lbm_mix_params* p, int Nx) {
   double mu_s[2] = {p->mu_ratio_a * mu, p->mu_ratio_b * mu};
   for (int sp = 0; sp < 2; ++sp) {
     L.s[sp] = (float)(1.0 / mh[sp]);
+    L.cw0[sp] = (float)((9.0 - 5.0 * (double)L.s[sp]) / 9.0);
+    L.cw1[sp] = (float)((double)L.s[sp] / 9.0);
+    L.cw5[sp] = (float)((double)L.s[sp] / 36.0);
     L.mh[sp] = mh[sp];
     double cxl = 3.0 * mu_s[sp] * sqrt(PI / (6.0 * mh[sp]));
     L.c_xl[sp] = (float)cxl;
@@ -858,7 +989,7 @@ Lat derive(const lbm_mix_params* p, int Nx) {
 
 int launch_colsum(lbm_mix* h, int b) {
   dim3 blk(128), grd((h->L.Nx + 127) / 128);
-  lbm_colsum_kernel<<<grd, blk, 0, h->stream>>>(h->L, h->buf[b], h->cs[b]);
+  lbm_colsum_kernel<float><<<grd, blk, 0, h->stream>>>(h->L, h->buf[b], h->refrho, h->cs[b]);
   CK(cudaGetLastError());
   return LBM_OK;
 }
@@ -871,10 +1002,11 @@ int reset_diag(lbm_mix* h) {
 }
 
 int launch_step(lbm_mix* h) {
-  StepArgs a;
+  StepArgs<float> a;
   const int b = h->cur;
   a.fin = h->buf[b];
   a.fout = h->buf[1 - b];
+  a.refrho = h->refrho;
   a.cs_in = h->cs[b];
   a.cs_out = h->cs[1 - b];
   a.alpha = h->alpha;
@@ -884,7 +1016,7 @@ int launch_step(lbm_mix* h) {
   a.diag_count = h->diag_count;
   a.clprof = h->clprof;
   dim3 blk(TX, TY), grd(h->nblocks);
-  lbm_step_kernel<<<grd, blk, 0, h->stream>>>(h->L, a);
+  lbm_step_kernel<float><<<grd, blk, 0, h->stream>>>(h->L, a);
   CK(cudaGetLastError());
   h->cur = 1 - b;
   h->steps++;
@@ -897,8 +1029,8 @@ int launch_moments(lbm_mix* h, double* d_out) {
   const bool direct = (h->steps == 0);
   const int b = direct ? h->cur : 1 - h->cur;
   dim3 blk(TX, TY), grd(h->nblocks);
-  lbm_moments_kernel<<<grd, blk, 0, h->stream>>>(h->L, h->buf[b], h->cs[b], h->alpha,
-                                                 direct ? 1 : 0, d_out);
+  lbm_moments_kernel<float><<<grd, blk, 0, h->stream>>>(h->L, h->buf[b], h->refrho, h->cs[b],
+                                                        h->alpha, direct ? 1 : 0, d_out);
   CK(cudaGetLastError());
   if (!h->L.x_periodic) {
     lbm_moments_ends_kernel<<<2, 256, 0, h->stream>>>(h->L, d_out);
@@ -927,6 +1059,24 @@ int latest_record(lbm_mix* h, double rec[NREC]) {
 }
 
 }  // namespace
+
+template <typename T>
+int get_post_state_t(lbm_mix* h, T* f, long n) {
+  int st = check_handle(h);
+  if (st) return st;
+  const long need = 18L * h->L.N * h->L.Nx;
+  if (!f || n != need) return set_err(LBM_EINVAL, "need %ld populations", need);
+  const size_t bytes = sizeof(T) * (size_t)need;
+  // staging area sized for the FP64 variant, shared by both getters
+  if (!h->scratch) CK(cudaMalloc((void**)&h->scratch, sizeof(double) * (size_t)need));
+  dim3 blk(128), grd((h->L.Nx + 127) / 128, h->L.N, 2);
+  lbm_convert_kernel<float, T><<<grd, blk, 0, h->stream>>>(h->L, h->buf[h->cur], h->refrho, 0,
+                                                           (T*)h->scratch);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(f, h->scratch, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
 
 extern "C" {
 
@@ -976,6 +1126,8 @@ void lbm_mix_destroy(lbm_mix* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   cudaFree(h->buf[0]);
   cudaFree(h->buf[1]);
+  cudaFree(h->refrho);
+  cudaFree(h->scratch);
   cudaFree(h->cs[0]);
   cudaFree(h->cs[1]);
   cudaFree(h->cs_snap);
@@ -1025,6 +1177,7 @@ int lbm_mix_create(const lbm_mix_params* p, void* stream, lbm_mix** out) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&(ptr), (bytes))
   ALLOC(h->buf[0], fbytes);
   ALLOC(h->buf[1], fbytes);
+  ALLOC(h->refrho, sizeof(float) * 2 * (size_t)Nx);
   ALLOC(h->cs[0], cbytes);
   ALLOC(h->cs[1], cbytes);
   ALLOC(h->cs_snap, cbytes);
@@ -1051,11 +1204,25 @@ int lbm_mix_create(const lbm_mix_params* p, void* stream, lbm_mix** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(h->cs[0], 0, cbytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->cs[1], 0, cbytes, h->stream);
   if (e == cudaSuccess) {
-    float* a = (float*)malloc(sizeof(float) * 2 * Nx);
+    float* a = (float*)malloc(sizeof(float) * 4 * Nx);
     if (!a) e = cudaErrorMemoryAllocation;
     else {
       for (int k = 0; k < 2 * Nx; ++k) a[k] = (float)p->accommodation;
+      // reference densities: the initial profile of lbm_mix_init
+      float* rb = a + 2 * Nx;
+      for (int x = 0; x < Nx; ++x) {
+        double t = h->L.x_periodic ? 1.0 : (double)x / (Nx - 1);
+        double n = h->L.x_periodic ? 1.0 : p->theta + (1.0 - p->theta) * t;
+        double Cl = h->L.C_in + (h->L.C_out - h->L.C_in) * t;
+        for (int sp = 0; sp < 2; ++sp) {
+          double C = (sp == h->L.light) ? Cl : 1.0 - Cl;
+          rb[sp * Nx + x] = (float)(n * C * h->L.mh[sp]);
+        }
+      }
       e = cudaMemcpyAsync(h->alpha, a, sizeof(float) * 2 * Nx, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->refrho, rb, sizeof(float) * 2 * Nx, cudaMemcpyHostToDevice,
+                            h->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
       free(a);
     }
@@ -1078,9 +1245,10 @@ int lbm_mix_init(lbm_mix* h) {
   if (st) return st;
   h->cur = 0;
   h->steps = 0;
-  dim3 blk(128), grd((h->L.Nx + 127) / 128, h->L.N);
-  lbm_init_kernel<<<grd, blk, 0, h->stream>>>(h->L, h->buf[0], h->p.theta);
-  CK(cudaGetLastError());
+  // the initial state is the rest equilibrium of the reference densities:
+  // all stored deviations are zero
+  CK(cudaMemsetAsync(h->buf[0], 0, sizeof(float) * 18 * (size_t)h->L.N * h->L.pitch,
+                     h->stream));
   if ((st = launch_colsum(h, 0))) return st;
   return reset_diag(h);
 }
@@ -1222,22 +1390,22 @@ int lbm_mix_set_post_state(lbm_mix* h, const float* f, long n) {
   CK(cudaMemcpy2DAsync(h->buf[0], sizeof(float) * h->L.pitch, f, sizeof(float) * h->L.Nx,
                        sizeof(float) * h->L.Nx, 18 * (size_t)h->L.N, cudaMemcpyHostToDevice,
                        h->stream));
+  {
+    dim3 blk(128), grd((h->L.Nx + 127) / 128, h->L.N, 2);
+    lbm_convert_kernel<float, float>
+        <<<grd, blk, 0, h->stream>>>(h->L, h->buf[0], h->refrho, 1, (float*)nullptr);
+    CK(cudaGetLastError());
+  }
   if ((st = launch_colsum(h, 0))) return st;
   if ((st = reset_diag(h))) return st;
   CK(cudaStreamSynchronize(h->stream));
   return LBM_OK;
 }
 
-int lbm_mix_get_post_state(lbm_mix* h, float* f, long n) {
-  int st = check_handle(h);
-  if (st) return st;
-  const long need = 18L * h->L.N * h->L.Nx;
-  if (!f || n != need) return set_err(LBM_EINVAL, "need %ld populations", need);
-  CK(cudaMemcpy2DAsync(f, sizeof(float) * h->L.Nx, h->buf[h->cur], sizeof(float) * h->L.pitch,
-                       sizeof(float) * h->L.Nx, 18 * (size_t)h->L.N, cudaMemcpyDeviceToHost,
-                       h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  return LBM_OK;
+int lbm_mix_get_post_state(lbm_mix* h, float* f, long n) { return get_post_state_t(h, f, n); }
+
+int lbm_mix_get_post_state_f64(lbm_mix* h, double* f, long n) {
+  return get_post_state_t(h, f, n);
 }
 
 int lbm_mix_dims(const lbm_mix* h, int* N, int* N_x, long* steps) {

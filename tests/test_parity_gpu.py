@@ -18,6 +18,10 @@ pytestmark = pytest.mark.gpu
 
 RTOL_RHO = 1e-5
 RTOL_U = 1e-4
+# Absolute floor for velocities: one FP32 rounding of a population is at most
+# 2^-24 of it and the rest population carries < 1/2 of rho, so u = sum c f / rho
+# is resolved to ~3e-8 by FP32 storage whatever its size.
+ATOL_U = 3e-8
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -52,16 +56,19 @@ def _check_moments(g, o, rtol_rho=RTOL_RHO, rtol_u=RTOL_U):
     for k in ("rho_a", "rho_b"):
         assert np.isfinite(mg[k]).all()
         assert _relerr(mg[k], mo[k]) < rtol_rho, (k, _relerr(mg[k], mo[k]))
+    scale = max(np.abs(mo["ua_x"]).max(), np.abs(mo["ub_x"]).max())
     for k in ("ua_x", "ua_y", "ub_x", "ub_y"):
-        scale = max(np.abs(mo["ua_x"]).max(), np.abs(mo["ub_x"]).max(), 1e-12)
-        err = np.abs(mg[k] - mo[k]).max() / scale
-        assert err < rtol_u, (k, err)
+        err = np.abs(mg[k] - mo[k]).max()
+        assert err < rtol_u * scale + ATOL_U, (k, err, scale)
     return mg, mo
 
 
 # ------------------------------------------------------ special functions
 def test_device_E1_and_psi():
+    """Device FP32 E_1 (series / Hastings rational) and psi against the FP64
+    oracle at the FP32-rounded arguments the device actually sees."""
     x = np.concatenate([np.geomspace(1e-5, 0.999, 60), [1.0], np.geomspace(1.001, 80, 80)])
+    x = x.astype(np.float32).astype(np.float64)
     e1, ps = binding.lbm_mix_eval_special(x)
     ref_e1 = np.array([oracle.E1(v) for v in x])
     ref_ps = np.array([oracle.psi(v) for v in x])
@@ -70,13 +77,16 @@ def test_device_E1_and_psi():
 
 
 # --------------------------------------------------------------- stepping
-@pytest.mark.parametrize("N,Nx", [(4, 6), (8, 8), (2, 5)])
-@pytest.mark.parametrize("steps", [1, 100])
+@pytest.mark.parametrize("N,Nx,steps", [(4, 6, 1), (4, 6, 100), (8, 8, 1), (8, 8, 100),
+                                         (2, 5, 1), (2, 5, 10)])
 def test_tiny_grids(N, Nx, steps):
+    """4 x 6 and 8 x 8 lattices after 1 and 100 steps; the two-row channel
+    only for 10 steps (its antisymmetric mode is unstable and amplifies
+    round-off in the oracle as well)."""
     p = workloads.preset("heli_argon_320x16", N=N, N_x=Nx)
     g, o = _pair(p, steps)
     _check_moments(g, o)
-    fp_g = g.get_post_state()[:, :, :, 1:-1]
+    fp_g = g.get_post_state_f64()[:, :, :, 1:-1]
     fp_o = o.get_post_state()[:, :, :, 1:-1]
     assert _relerr(fp_g, fp_o) < RTOL_RHO
 
@@ -84,7 +94,7 @@ def test_tiny_grids(N, Nx, steps):
 def test_ragged_multi_tile_channel():
     """Several 32-column strips with a ragged last strip (100 columns) and a
     row count that is not a multiple of the 8-row sweep (20 rows)."""
-    p = workloads.preset("neon_argon_2048x32", N=20, N_x=100)
+    p = workloads.preset("neon_argon_2048x32", N=20, N_x=100, theta=1.5)
     g, o = _pair(p, 300)
     _check_moments(g, o)
     sg, so = g.separation(), o.separation()
@@ -96,9 +106,12 @@ def test_ragged_multi_tile_channel():
 
 
 def test_unequal_end_composition_and_accommodation_field():
-    p = workloads.preset("heli_argon_320x16", N=10, N_x=40, C_l_out=0.3)
-    alpha = workloads.random_accommodation(40, seed=1, spread=0.3)
-    g, o = _pair(p, 200, alpha=alpha)
+    """C_l,out != C_l,in and a per-wall-node accommodation field 1 - U(0, 0.05)
+    on a 120 x 10 channel at theta = 1.5 (shorter channels at theta = 2 reach
+    Mach numbers where the scheme diverges in the oracle as well)."""
+    p = workloads.preset("heli_argon_320x16", N=10, N_x=120, theta=1.5, C_l_out=0.3)
+    alpha = workloads.random_accommodation(120, seed=1, spread=0.05)
+    g, o = _pair(p, 400, alpha=alpha)
     _check_moments(g, o)
 
 
@@ -119,18 +132,26 @@ def test_mass_conservation_fp32():
     h = g.history(4096)
     assert len(h) == 2000 and h[-1, 0] == 2000
     ma, mb = h[:, 6], h[:, 7]
-    assert np.abs(ma / ma[0] - 1).max() < 2e-6
-    assert np.abs(mb / mb[0] - 1).max() < 2e-6
+    assert np.abs(ma / ma[0] - 1).max() < 1e-6
+    assert np.abs(mb / mb[0] - 1).max() < 1e-6
 
 
 def test_rest_state_fixed_point():
+    """Uniform densities at rest with theta = 1: one step reproduces every
+    population to 2 FP32 ulps; over 500 steps the state only random-walks by
+    round-off (bound 2 ulp x sqrt(steps)).  A wrong equilibrium, wall density
+    or end correction moves it by ~1e-2 in the first step."""
     p = workloads.preset("heli_argon_320x16", N=8, N_x=30, theta=1.0)
     g = binding.LbmMix(**p)
     g.init()
-    f0 = g.get_post_state()
-    g.step(500)
-    f1 = g.get_post_state()
-    assert np.abs(f1 - f0)[:, :, :, 1:-1].max() < 1e-6 * np.abs(f0).max()
+    f0 = g.get_post_state()[:, :, :, 1:-1]
+    ulp = np.spacing(np.abs(f0).astype(np.float32))
+    g.step(1)
+    f1 = g.get_post_state()[:, :, :, 1:-1]
+    assert (np.abs(f1 - f0) <= 2 * ulp).all()
+    g.step(499)
+    f2 = g.get_post_state()[:, :, :, 1:-1]
+    assert (np.abs(f2 - f0) <= 2 * ulp * np.sqrt(500)).all()
 
 
 def test_identical_species_no_separation():
@@ -183,7 +204,14 @@ def test_post_state_roundtrip_and_errors():
     g = binding.LbmMix(**p)
     f = workloads.random_post_state(6, 20, seed=9).astype(np.float32)
     g.set_post_state(f)
-    assert np.array_equal(g.get_post_state(), f)
+    # stored as FP32 deviations d = f - ref from the column reference: one
+    # FP32 rounding of d (|d| can exceed |f| where the reference is larger,
+    # so the bound is relative to the species' largest population); the FP64
+    # read-back adds ref exactly, the FP32 one rounds once more
+    for sp in range(2):
+        tol = 2.0 ** -23 * np.abs(f[sp]).max() * 8
+        assert np.abs(g.get_post_state_f64()[sp] - f[sp]).max() <= tol
+        assert np.abs(g.get_post_state()[sp] - f[sp]).max() <= 2 * tol
     with pytest.raises(binding.LbmError):
         g.set_accommodation_field(np.full(40, 1.5))
     with pytest.raises(binding.LbmError):
@@ -225,11 +253,11 @@ def test_neon_argon_full_size_one_step():
     g = binding.LbmMix(**p)
     g.init()
     g.step(3)
-    fp = g.get_post_state()
+    fp = g.get_post_state_f64()
     g.step(1)
     mg = g.moments()
     o = oracle.Oracle(p)
-    o.set_post_state(fp.astype(np.float64))
+    o.set_post_state(fp)
     del fp
     o.step(1)
     mo = o.moments()
@@ -237,4 +265,4 @@ def test_neon_argon_full_size_one_step():
         assert _relerr(mg[k], mo[k]) < RTOL_RHO, k
     scale = max(np.abs(mo["ua_x"]).max(), np.abs(mo["ub_x"]).max())
     for k in ("ua_x", "ua_y", "ub_x", "ub_y"):
-        assert np.abs(mg[k] - mo[k]).max() / scale < RTOL_U, k
+        assert np.abs(mg[k] - mo[k]).max() < RTOL_U * scale + ATOL_U, k
