@@ -11,11 +11,17 @@
 // that feed the next step's density correction and the separation
 // diagnostics (Eqs. C, CL, Clline).
 //
-// Data layout in HBM (per buffer): f[species][i][row][column], FP32, row
-// pitch padded to 32 floats (128 B); two buffers A/B alternate.  One CTA owns
-// a strip of 32 columns over ALL rows, sweeping rows in steps of TY, so that
-// every per-column quantity (the tau_q of the two walls, the column sums) is
-// produced inside one CTA without atomics and in a fixed order.
+// Data layout in HBM (per buffer): the channel is cut into strips of 32
+// columns; strip s holds, row after row, the 18 populations (species a then
+// b, i = 0..8) of its 32 columns as 128-byte segments:
+//   offset(sp, i, j, x) = (x / 32) * SS + j * RS + (sp * 9 + i) * 32 + x % 32
+// with RS = 576 floats per row block and SS = N * RS per strip.  A strip is
+// one contiguous region that its CTA streams through front to back, every
+// warp access is one aligned 128-byte segment, and all offsets inside a strip
+// are compile-time immediates.  Two buffers A/B alternate.  One CTA owns one
+// strip over ALL rows, sweeping rows in steps of TY, so that every per-column
+// quantity (the tau_q of the two walls, the column sums) is produced inside
+// one CTA without atomics and in a fixed order.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -51,7 +57,8 @@ int set_err(int code, const char* fmt, ...) {
   } while (0)
 
 // ------------------------------------------------------- lattice constants
-constexpr int TX = 32;          // columns per CTA (one warp per row segment)
+constexpr int TX = 32;          // columns per CTA = strip width (one warp per row segment)
+constexpr int RS = 18 * TX;     // floats per row block of a strip
 constexpr int TY = 8;           // rows per sweep iteration
 constexpr int NPART = 8;        // doubles per CTA partial
 constexpr int NREC = 8;         // doubles per diagnostic record
@@ -60,8 +67,7 @@ constexpr float kPi = 3.14159265358979323846f;
 
 struct Lat {
   int N, Nx, pitch;
-  unsigned pop_stride;   // N * pitch
-  unsigned spec_stride;  // 9 * pop_stride
+  unsigned SS;           // floats per strip: N * RS
   int x_periodic;
   int light;             // index of the light species
   float s[2];            // s_sigma = m_min / m_sigma
@@ -176,10 +182,14 @@ struct Ends {
   float gin[2], gout[2];  // ghost reference offsets kappa(2 rb(1) - rb(2)) - rb(0), per species
 };
 
+__device__ __forceinline__ unsigned idx(const Lat& L, int sp, int i, int j, int x) {
+  return (unsigned)(x >> 5) * L.SS + (unsigned)(j * RS + (sp * 9 + i) * TX + (x & 31));
+}
+
 template <typename ST>
 __device__ __forceinline__ float ld(const ST* __restrict__ f, const Lat& L, int sp, int i, int j,
                                     int x) {
-  return Stor<ST>::ld(f + sp * L.spec_stride + i * L.pop_stride + j * L.pitch + x);
+  return Stor<ST>::ld(f + idx(L, sp, i, j, x));
 }
 
 // Deviation (relative to the SOURCE column's reference) that population i
@@ -272,6 +282,30 @@ __device__ __forceinline__ void pull_node(const ST* __restrict__ f, const Lat& L
       g[7] = fmaf(c5, dr, src(f, L, E, c5, sp, 7, j + 1, xp));
       g[8] = fmaf(c5, dl, src(f, L, E, c5, sp, 8, j + 1, xm));
     }
+  }
+}
+
+// The same pull for a node whose row is not a wall row and whose strip does
+// not contain an end column: nine plain loads per species at immediate
+// offsets from the row pointers of columns x (p), x - 1 (pl) and x + 1 (pr).
+template <typename ST>
+__device__ __forceinline__ void pull_fast(const ST* __restrict__ p, const ST* __restrict__ pl,
+                                          const ST* __restrict__ pr, const Lat& L,
+                                          const ColRef& C, float fs[2][9]) {
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    const int o = sp * 9 * TX;
+    const float c1 = L.cw1[sp], c5 = L.cw5[sp], dl = C.dl[sp], dr = C.dr[sp];
+    float* g = fs[sp];
+    g[0] = Stor<ST>::ld(p + o);
+    g[1] = fmaf(c1, dl, Stor<ST>::ld(pl + o + 1 * TX));
+    g[3] = fmaf(c1, dr, Stor<ST>::ld(pr + o + 3 * TX));
+    g[2] = Stor<ST>::ld(p + o + 2 * TX - RS);
+    g[5] = fmaf(c5, dl, Stor<ST>::ld(pl + o + 5 * TX - RS));
+    g[6] = fmaf(c5, dr, Stor<ST>::ld(pr + o + 6 * TX - RS));
+    g[4] = Stor<ST>::ld(p + o + 4 * TX + RS);
+    g[7] = fmaf(c5, dr, Stor<ST>::ld(pr + o + 7 * TX + RS));
+    g[8] = fmaf(c5, dl, Stor<ST>::ld(pl + o + 8 * TX + RS));
   }
 }
 
@@ -513,6 +547,9 @@ struct StepArgs {
   double* __restrict__ diag;         // [DIAG_CAP][NREC]
   unsigned long long* __restrict__ diag_count;
   double* __restrict__ clprof;       // [Nx]
+  double* __restrict__ colpart;      // [R][4][Nx] per-row-block column sums (R > 1)
+  unsigned* __restrict__ strip_cnt;  // [strips] row blocks finished this step
+  int rows_per_block;                // rows of one row block (multiple of TY)
 };
 
 struct RedSmem {
@@ -521,6 +558,7 @@ struct RedSmem {
   double wmin[TY];
   int wimin[TY];
   int last;
+  int last_strip;
 };
 
 // Warp-level FP64 sum and (min, argmin) with ties to the smaller column.
@@ -548,17 +586,48 @@ __device__ __forceinline__ void column_epilogue(const Lat& L, const StepArgs<ST>
                                                 const double acc[4], RedSmem& rs) {
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * TX + tx;
+  const int R = gridDim.y;  // row blocks per strip
 #pragma unroll
   for (int k = 0; k < 4; ++k) rs.col[k][ty][tx] = acc[k];
   __syncthreads();
+  double c[4];
   if (ty == 0) {
-    double c[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       double v = 0.0;
       for (int t = 0; t < TY; ++t) v += rs.col[k][t][tx];
       c[k] = v;
     }
+  }
+  if (R > 1) {
+    // Row-block partials of this strip; the last of its R CTAs to finish
+    // adds them in row-block order (independent of arrival order).
+    if (ty == 0 && x < L.Nx) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        a.colpart[((size_t)blockIdx.y * 4 + k) * L.Nx + x] = c[k];
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      unsigned ticket = atomicAdd(a.strip_cnt + blockIdx.x, 1u);
+      rs.last_strip = (ticket == (unsigned)R - 1u);
+    }
+    __syncthreads();
+    if (!rs.last_strip) return;
+    __threadfence();
+    if (ty == 0) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        double v = 0.0;
+        if (x < L.Nx)
+          for (int r = 0; r < R; ++r) v += __ldcg(a.colpart + ((size_t)r * 4 + k) * L.Nx + x);
+        c[k] = v;
+      }
+      if (tx == 0) a.strip_cnt[blockIdx.x] = 0u;
+    }
+  }
+  if (ty == 0) {
     const bool in = interior(L, x);
     if (x < L.Nx) {
 #pragma unroll
@@ -665,41 +734,55 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
   __shared__ WallSmem wsm;
   __shared__ RedSmem rsm;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x = blockIdx.x * TX + tx;
+  const int x0 = blockIdx.x * TX, x = x0 + tx;
   const ColRef C = col_ref(L, a.refrho, x);
   const Ends E = load_ends(L, a.cs_in, a.refrho);
   wall_prologue<true>(L, a.fin, a.alpha, E, C, x, wsm);
   const bool in = interior(L, x);
+  // strips holding column 1 or N_x - 2 take the general pull (ghost columns)
+  const bool edge_strip = !L.x_periodic && (x0 <= 1 || x0 + TX > L.Nx - 2);
+  int xm = x - 1, xp = x + 1;
+  if (xm < 0) xm += L.Nx;
+  if (xp >= L.Nx) xp -= L.Nx;
+  const unsigned base = blockIdx.x * L.SS + tx;  // row 0, species a, i = 0 of column x
+  const int offl = (int)(idx(L, 0, 0, 0, xm) - base), offr = (int)(idx(L, 0, 0, 0, xp) - base);
   const float r_bot = wsm.r[0][tx], r_top = wsm.r[1][tx];
   const int half = (L.N + 1) / 2;  // rows j < half (1-based 2J <= N+1) use the bottom tau_q
   KahanF acc[4];
+  const int j_begin = blockIdx.y * a.rows_per_block;
+  const int j_end = min(L.N, j_begin + a.rows_per_block);
   if (in) {
-    for (int j = ty; j < L.N; j += TY) {
+    for (int j = j_begin + ty; j < j_end; j += TY) {
       float fs[2][9];
-      pull_node(a.fin, L, E, C, x, j, r_bot, r_top, fs);
+      const ST* p = a.fin + base + j * RS;
+      if (!edge_strip && j != 0 && j != L.N - 1)
+        pull_fast(p, p + offl, p + offr, L, C, fs);
+      else
+        pull_node(a.fin, L, E, C, x, j, r_bot, r_top, fs);
       Macro m;
       macro(L, C, fs, m);
       float om_s, om_d;
       rates(L, m, (float)j + 0.5f, om_s, om_d);
       const float om_q = wsm.om_q[j < half ? 0 : 1][tx];
+      ST* o = a.fout + base + j * RS;
 #pragma unroll
       for (int sp = 0; sp < 2; ++sp) {
         float mxs = collide(fs[sp], m.rho[sp], L.s[sp], m.ux, m.uy, L.om_e, L.om_eps, om_d,
                             om_q, om_s);
         acc[sp].add(m.sd[sp]);
         acc[2 + sp].add(mxs);
-        ST* o = a.fout + sp * L.spec_stride + j * L.pitch + x;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) Stor<ST>::st(o + i * L.pop_stride, fs[sp][i]);
+        for (int i = 0; i < 9; ++i) Stor<ST>::st(o + (sp * 9 + i) * TX, fs[sp][i]);
       }
     }
   }
   // column sum of rho_s = N rhobar_s + sum of deviations; the reference part
-  // is added once per column (by the ty = 0 thread of the strip)
+  // is added once per column (by the ty = 0 thread of the first row block)
+  const bool adds_ref = in && ty == 0 && blockIdx.y == 0;
   double accd[4];
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp)
-    accd[sp] = (in && ty == 0 ? (double)L.N * (double)C.rb[sp] : 0.0) + acc[sp].value();
+    accd[sp] = (adds_ref ? (double)L.N * (double)C.rb[sp] : 0.0) + acc[sp].value();
   accd[2] = acc[2].value();
   accd[3] = acc[3].value();
   column_epilogue(L, a, x, accd, rsm);
@@ -808,12 +891,12 @@ __global__ void lbm_colsum_kernel(Lat L, const ST* __restrict__ f,
   }
 }
 
-// Full populations <-> stored deviations: to_dev = 1 converts f (already in
-// the buffer, FP32) into deviations in place; to_dev = 0 writes
-// f = d + ref into out (T = float or double, unpadded [2][9][N][Nx]).
+// Full populations <-> stored deviations.  to_dev = 1: reads f from `in`
+// (FP32, unpadded [2][9][N][Nx]) and stores d = f - ref in the strip layout;
+// to_dev = 0: writes f = d + ref to `out` (T = float or double, unpadded).
 template <typename ST, typename T>
 __global__ void lbm_convert_kernel(Lat L, ST* __restrict__ f, const float* __restrict__ refrho,
-                                   int to_dev, T* __restrict__ out) {
+                                   int to_dev, const float* __restrict__ in, T* __restrict__ out) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y, sp = blockIdx.z;
   if (x >= L.Nx) return;
@@ -821,12 +904,12 @@ __global__ void lbm_convert_kernel(Lat L, ST* __restrict__ f, const float* __res
   for (int i = 0; i < 9; ++i) {
     const float cw = i == 0 ? L.cw0[sp] : (i < 5 ? L.cw1[sp] : L.cw5[sp]);
     const float ref = cw * rb;
-    ST* p = f + sp * L.spec_stride + i * L.pop_stride + j * L.pitch + x;
-    if (to_dev) {
-      Stor<ST>::st(p, (float)*p - ref);
-    } else {
-      out[(((size_t)sp * 9 + i) * L.N + j) * L.Nx + x] = (T)Stor<ST>::ld(p) + (T)ref;
-    }
+    ST* p = f + idx(L, sp, i, j, x);
+    const size_t h = (((size_t)sp * 9 + i) * L.N + j) * L.Nx + x;
+    if (to_dev)
+      Stor<ST>::st(p, in[h] - ref);
+    else
+      out[h] = (T)Stor<ST>::ld(p) + (T)ref;
   }
 }
 
@@ -891,6 +974,9 @@ struct lbm_mix {
   double* diag;
   unsigned long long* diag_count;
   double* clprof;
+  double* colpart;     // [R][4][Nx]
+  unsigned* strip_cnt; // [nblocks]
+  int R, rows_per_block;
   double* resid;
   double* mom;
   double* h_pinned;  // small pinned staging area
@@ -944,8 +1030,7 @@ Lat derive(const lbm_mix_params* p, int Nx) {
   L.N = p->N;
   L.Nx = Nx;
   L.pitch = (Nx + 31) / 32 * 32;
-  L.pop_stride = (unsigned)((long)L.N * L.pitch);
-  L.spec_stride = 9u * L.pop_stride;
+  L.SS = (unsigned)((long)L.N * RS);
   L.x_periodic = p->x_periodic;
   double m_min = fmin(p->m_a, p->m_b);
   double mh[2] = {p->m_a / m_min, p->m_b / m_min};
@@ -1015,7 +1100,10 @@ int launch_step(lbm_mix* h) {
   a.diag = h->diag;
   a.diag_count = h->diag_count;
   a.clprof = h->clprof;
-  dim3 blk(TX, TY), grd(h->nblocks);
+  a.colpart = h->colpart;
+  a.strip_cnt = h->strip_cnt;
+  a.rows_per_block = h->rows_per_block;
+  dim3 blk(TX, TY), grd(h->nblocks, h->R);
   lbm_step_kernel<float><<<grd, blk, 0, h->stream>>>(h->L, a);
   CK(cudaGetLastError());
   h->cur = 1 - b;
@@ -1071,7 +1159,7 @@ int get_post_state_t(lbm_mix* h, T* f, long n) {
   if (!h->scratch) CK(cudaMalloc((void**)&h->scratch, sizeof(double) * (size_t)need));
   dim3 blk(128), grd((h->L.Nx + 127) / 128, h->L.N, 2);
   lbm_convert_kernel<float, T><<<grd, blk, 0, h->stream>>>(h->L, h->buf[h->cur], h->refrho, 0,
-                                                           (T*)h->scratch);
+                                                           nullptr, (T*)h->scratch);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(f, h->scratch, bytes, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -1137,6 +1225,8 @@ void lbm_mix_destroy(lbm_mix* h) {
   cudaFree(h->diag);
   cudaFree(h->diag_count);
   cudaFree(h->clprof);
+  cudaFree(h->colpart);
+  cudaFree(h->strip_cnt);
   cudaFree(h->resid);
   cudaFree(h->mom);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
@@ -1187,6 +1277,14 @@ int lbm_mix_create(const lbm_mix_params* p, void* stream, lbm_mix** out) {
   ALLOC(h->diag, sizeof(double) * DIAG_CAP * NREC);
   ALLOC(h->diag_count, sizeof(unsigned long long));
   ALLOC(h->clprof, sizeof(double) * (size_t)Nx);
+  // Row blocks: split each strip's rows over R CTAs of ~128 rows so that the
+  // grid holds several waves of CTAs on 152 SMs (one strip per CTA leaves a
+  // partly empty last wave for the 1024-strip channel).
+  h->R = (h->L.N + 127) / 128;
+  h->rows_per_block = ((h->L.N + h->R - 1) / h->R + TY - 1) / TY * TY;
+  h->R = (h->L.N + h->rows_per_block - 1) / h->rows_per_block;
+  ALLOC(h->colpart, sizeof(double) * 4 * (size_t)Nx * (size_t)h->R);
+  ALLOC(h->strip_cnt, sizeof(unsigned) * (size_t)h->nblocks);
   ALLOC(h->resid, sizeof(double));
 #undef ALLOC
   if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_pinned, sizeof(double) * 64);
@@ -1201,6 +1299,8 @@ int lbm_mix_create(const lbm_mix_params* p, void* stream, lbm_mix** out) {
   e = cudaMemsetAsync(h->buf[0], 0, fbytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, fbytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->counter, 0, sizeof(unsigned), h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->strip_cnt, 0, sizeof(unsigned) * (size_t)h->nblocks, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->cs[0], 0, cbytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->cs[1], 0, cbytes, h->stream);
   if (e == cudaSuccess) {
@@ -1387,13 +1487,13 @@ int lbm_mix_set_post_state(lbm_mix* h, const float* f, long n) {
   if (!f || n != need) return set_err(LBM_EINVAL, "need %ld populations", need);
   h->cur = 0;
   h->steps = 0;
-  CK(cudaMemcpy2DAsync(h->buf[0], sizeof(float) * h->L.pitch, f, sizeof(float) * h->L.Nx,
-                       sizeof(float) * h->L.Nx, 18 * (size_t)h->L.N, cudaMemcpyHostToDevice,
-                       h->stream));
+  if (!h->scratch) CK(cudaMalloc((void**)&h->scratch, sizeof(double) * (size_t)need));
+  CK(cudaMemcpyAsync(h->scratch, f, sizeof(float) * (size_t)need, cudaMemcpyHostToDevice,
+                     h->stream));
   {
     dim3 blk(128), grd((h->L.Nx + 127) / 128, h->L.N, 2);
-    lbm_convert_kernel<float, float>
-        <<<grd, blk, 0, h->stream>>>(h->L, h->buf[0], h->refrho, 1, (float*)nullptr);
+    lbm_convert_kernel<float, float><<<grd, blk, 0, h->stream>>>(
+        h->L, h->buf[0], h->refrho, 1, (const float*)h->scratch, (float*)nullptr);
     CK(cudaGetLastError());
   }
   if ((st = launch_colsum(h, 0))) return st;

@@ -105,6 +105,17 @@ def test_ragged_multi_tile_channel():
     assert np.abs(sg["Cl_profile"] - so["Cl_profile"]).max() < 1e-6
 
 
+def test_row_blocks_and_tall_channel():
+    """A 260-row channel is split into three row blocks per strip (88, 88 and
+    84 rows) whose column sums meet in a second-level reduction."""
+    p = workloads.preset("neon_argon_2048x32", N=260, N_x=70, theta=1.2, Kn_out=0.02)
+    g, o = _pair(p, 60)
+    _check_moments(g, o)
+    sg, so = g.separation(), o.separation()
+    assert np.abs(sg["Cl_profile"] - so["Cl_profile"]).max() < 1e-6
+    assert abs(sg["mdot_a"] / so["mdot_a"] - 1) < RTOL_U
+
+
 def test_unequal_end_composition_and_accommodation_field():
     """C_l,out != C_l,in and a per-wall-node accommodation field 1 - U(0, 0.05)
     on a 120 x 10 channel at theta = 1.5 (shorter channels at theta = 2 reach
