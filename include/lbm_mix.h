@@ -163,6 +163,49 @@ int lbm_mix_sync(lbm_mix* h);
  * functions; uses its own temporary device memory. */
 int lbm_mix_eval_special(const double* x, double* e1, double* psi, long n);
 
+/* One time step with no device allocation, for callers that cannot call
+ * cudaMalloc (for example code that owns a fixed device-memory budget, runs
+ * under an allocator it does not control, or must not allocate while a CUDA
+ * graph it belongs to is being captured).  This entry point has no
+ * counterpart in the paper; it runs the same fused step kernel as
+ * lbm_mix_step, with the kernel's scratch (per-strip partial sums and the
+ * arrival tickets of its two-level reduction) in a static device array of
+ * 69 KB that every GPU loading the library holds until the process exits.
+ * That array covers N_x <= 32768 columns; larger N_x is rejected with
+ * LBM_EINVAL.  The step runs with one row block per strip.
+ *
+ * All buffers are caller-owned DEVICE memory, read or written on `stream`
+ * (a cudaStream_t, NULL for the legacy default stream):
+ *   d_in, d_out   post-collision populations before and after the step, as
+ *                 FP32 deviations d = f - w_i alpha_si rhobar_s(x) from the
+ *                 rest equilibrium (Eq. feq with u = 0; w_i alpha_si =
+ *                 (9 - 5 s)/9, s/9, s/36 for rest, axis, diagonal
+ *                 populations, s = m_min / m_sigma) of the reference density
+ *                 rhobar; laid out in strips of 32 columns:
+ *                 index = (x/32) * 576 N + j * 576 + (sigma * 9 + i) * 32 + x%32,
+ *                 18 * N * 32 * ceil(N_x/32) floats each; must not alias;
+ *   d_refrho      rhobar_s(x), [2][N_x] floats, any fixed positive profile
+ *                 (the same one for every step of a run);
+ *   d_alpha       accommodation coefficients, [2][N_x] floats (bottom, top);
+ *   d_colsum_in   [4][N_x] doubles: column sums sum_j rho_a, sum_j rho_b of
+ *                 the state in d_in (rows 2 and 3 are not read);
+ *   d_colsum_out  [4][N_x] doubles written: sum_j rho_a, sum_j rho_b,
+ *                 sum_j rho_a u_a,x, sum_j rho_b u_b,x of the new state;
+ *   d_record      8 doubles written: {1, CL, C~_l, mdot_a, mdot_b, x_min,
+ *                 total mass a, total mass b} of the new state;
+ *   d_cl_profile  N_x doubles written: C_l(x) of the new state.
+ * The first call on a device looks up the static array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one array and resets its counters, so calls whose
+ * kernels overlap on the GPU (different streams, or different threads
+ * without ordering) race and corrupt each other's results; serialise them.
+ * Returns LBM_OK once the step is enqueued, LBM_EINVAL for bad parameters,
+ * pointers or sizes, LBM_ECUDA for launch errors. */
+int lbm_mix_step_noalloc(const lbm_mix_params* p, const float* d_in, float* d_out,
+                         const float* d_refrho, const float* d_alpha, const double* d_colsum_in,
+                         double* d_colsum_out, double* d_record, double* d_cl_profile,
+                         void* stream);
+
 /* Static description of an error code; never NULL. */
 const char* lbm_mix_strerror(int status);
 

@@ -74,6 +74,7 @@ _SIGS = {
     "lbm_mix_dims": (_I, [_H, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_L)]),
     "lbm_mix_sync": (_I, [_H]),
     "lbm_mix_eval_special": (_I, [_PD, _PD, _PD, _L]),
+    "lbm_mix_step_noalloc": (_I, [ctypes.POINTER(lbm_mix_params)] + [ctypes.c_void_p] * 9),
     "lbm_mix_strerror": (ctypes.c_char_p, [_I]),
     "lbm_mix_last_error": (ctypes.c_char_p, []),
 }
@@ -237,6 +238,18 @@ def lbm_mix_eval_special(x: np.ndarray):
     _check(load().lbm_mix_eval_special(_dptr(x), _dptr(e1), _dptr(ps), x.size),
            "lbm_mix_eval_special")
     return e1, ps
+
+
+def lbm_mix_step_noalloc(params: lbm_mix_params, d_in: int, d_out: int, d_refrho: int,
+                         d_alpha: int, d_colsum_in: int, d_colsum_out: int, d_record: int,
+                         d_cl_profile: int, stream=None) -> None:
+    """One allocation-free step on caller-owned device buffers (integer
+    device addresses, e.g. torch ``data_ptr()``); see include/lbm_mix.h."""
+    ptrs = [d_in, d_out, d_refrho, d_alpha, d_colsum_in, d_colsum_out, d_record, d_cl_profile]
+    _check(load().lbm_mix_step_noalloc(ctypes.byref(params),
+                                       *[ctypes.c_void_p(int(q)) for q in ptrs],
+                                       ctypes.c_void_p(_stream_handle(stream))),
+           "lbm_mix_step_noalloc")
 
 
 def lbm_mix_strerror(status: int) -> str:

@@ -30,6 +30,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "../../include/lbm_mix.h"
@@ -1148,6 +1149,41 @@ int latest_record(lbm_mix* h, double rec[NREC]) {
 
 }  // namespace
 
+// ---------------------------------------------- allocation-free stepping
+// Scratch of lbm_mix_step_noalloc: the per-strip partial sums, the per-strip
+// and grid arrival tickets and the record counter of lbm_step_kernel, in one
+// static device array so that a caller who cannot allocate device memory can
+// still run a step.  Every GPU that loads the library holds it until exit:
+//   partials  NOALLOC_MAX_STRIPS * NPART doubles   (64 KiB)
+//   counters  NOALLOC_MAX_STRIPS + 4 words          (4 KiB + 16 B)
+constexpr int NOALLOC_MAX_STRIPS = 1024;  // N_x <= 32 * 1024 = 32768 columns
+constexpr size_t NOALLOC_PART_DOUBLES = (size_t)NOALLOC_MAX_STRIPS * NPART;
+constexpr size_t NOALLOC_CNT_WORDS = NOALLOC_MAX_STRIPS + 4;
+constexpr size_t NOALLOC_DOUBLES = NOALLOC_PART_DOUBLES + (NOALLOC_CNT_WORDS + 1) / 2;
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+// Device address of g_noalloc_scratch for the current device, looked up once
+// per device.  In host code the symbol's name only stands for the device
+// array; kernels must be given this address.
+int noalloc_scratch_address(double** out) {
+  static std::mutex mu;
+  static double* addr[64] = {};
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_err(LBM_EINVAL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+      return set_err(LBM_ECUDA, "cudaGetSymbolAddress(scratch) failed on device %d: %s", dev,
+                     cudaGetErrorString(e));
+    addr[dev] = (double*)ptr;
+  }
+  *out = addr[dev];
+  return LBM_OK;
+}
+
 template <typename T>
 int get_post_state_t(lbm_mix* h, T* f, long n) {
   int st = check_handle(h);
@@ -1545,6 +1581,52 @@ int lbm_mix_eval_special(const double* x, double* e1, double* psi, long n) {
   cudaFree(de);
   cudaFree(dp);
   if (e != cudaSuccess) return set_err(LBM_ECUDA, "eval_special: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int lbm_mix_step_noalloc(const lbm_mix_params* p, const float* d_in, float* d_out,
+                         const float* d_refrho, const float* d_alpha, const double* d_colsum_in,
+                         double* d_colsum_out, double* d_record, double* d_cl_profile,
+                         void* stream) {
+  int Nx = 0;
+  int st = validate(p, &Nx);
+  if (st != LBM_OK) return st;
+  if (!d_in || !d_out || !d_refrho || !d_alpha || !d_colsum_in || !d_colsum_out || !d_record ||
+      !d_cl_profile)
+    return set_err(LBM_EINVAL, "lbm_mix_step_noalloc: every buffer must be a device pointer");
+  if (d_in == d_out) return set_err(LBM_EINVAL, "lbm_mix_step_noalloc: d_in and d_out alias");
+  const int nstrips = (Nx + TX - 1) / TX;
+  if (nstrips > NOALLOC_MAX_STRIPS)
+    return set_err(LBM_EINVAL,
+                   "lbm_mix_step_noalloc: N_x = %d exceeds the %d columns its static scratch "
+                   "covers",
+                   Nx, NOALLOC_MAX_STRIPS * TX);
+  double* scratch = nullptr;
+  if ((st = noalloc_scratch_address(&scratch))) return st;
+  const Lat L = derive(p, Nx);
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* cnt = (unsigned*)(scratch + NOALLOC_PART_DOUBLES);
+  // tickets and the record counter must start at zero; the partials are
+  // overwritten before they are read
+  CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * NOALLOC_CNT_WORDS, s));
+  StepArgs<float> a;
+  a.fin = d_in;
+  a.fout = d_out;
+  a.refrho = d_refrho;
+  a.cs_in = d_colsum_in;
+  a.cs_out = d_colsum_out;
+  a.alpha = d_alpha;
+  a.partials = scratch;
+  a.strip_cnt = cnt;
+  a.counter = cnt + NOALLOC_MAX_STRIPS;
+  a.diag_count = (unsigned long long*)(cnt + NOALLOC_MAX_STRIPS + 2);
+  a.diag = d_record;  // the zeroed counter puts the record at index 0
+  a.clprof = d_cl_profile;
+  a.colpart = nullptr;  // one row block per strip: no row-block partials
+  a.rows_per_block = (L.N + TY - 1) / TY * TY;
+  dim3 blk(TX, TY), grd(nstrips, 1);
+  lbm_step_kernel<float><<<grd, blk, 0, s>>>(L, a);
+  CK(cudaGetLastError());
   return LBM_OK;
 }
 
