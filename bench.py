@@ -184,7 +184,7 @@ def run_ours(args):
 
     from paper_1603_08221_gb300 import binding, workloads
     binding.load()
-    p = workloads.preset(args.workload)
+    p = workloads.preset(args.workload, diag_every=args.diag_every)
     # a dedicated (non-default) stream: the library and the CUDA events below
     # must see the same stream
     stream = torch.cuda.Stream(dev)
@@ -263,6 +263,7 @@ def run_ours(args):
                    "m_a": p["m_a"], "m_b": p["m_b"], "C_l": p["C_l"], "theta": p["theta"],
                    "Kn_out": p["Kn_out"], "nodes_updated": nodes,
                    "bytes_per_node_step": BYTES_PER_NODE,
+                   "diag_every": args.diag_every,
                    "l2": "state (2 x 1.2 GB FP32) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -290,6 +291,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-steps", type=int, default=100)
+    ap.add_argument("--diag-every", type=int, default=100,
+                    help="steps between FP64 separation-diagnostic reductions (the column "
+                         "sums of the end columns are reduced every step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -63,12 +63,13 @@ typedef struct {
   double mu_ratio_a, mu_ratio_b;  /* mu_sigma / mu of the mixture */
   int storage;          /* LBM_FP32 */
   int x_periodic;       /* 1: periodic in x instead of pressure ends */
+  int diag_every;       /* >= 1: steps between separation-diagnostic reductions */
 } lbm_mix_params;
 
 /* Fills the defaults: He-Ar (4.003, 39.948), C_l = 0.5, C_l_out = -1,
  * theta = 2, Kn_out = 0.1, N = 16, N_x = 0, L_over_H = 20, alpha = 1,
  * c_m0 = 1.016, tau_rho = 1, tau_e = 1.1, tau_eps = 1.2, mu ratios 1,
- * LBM_FP32, x_periodic = 0.  NULL-safe. */
+ * LBM_FP32, x_periodic = 0, diag_every = 1.  NULL-safe. */
 void lbm_mix_default_params(lbm_mix_params* p);
 
 /* Validates p, derives the lattice constants (Eqs. P, EQFrb, rho2 with the
@@ -89,8 +90,11 @@ void lbm_mix_destroy(lbm_mix* h);
 int lbm_mix_init(lbm_mix* h);
 
 /* Advances nsteps >= 0 time steps (Eq. MRT), one fused collide-stream pass
- * per step on the handle's stream, asynchronously.  Each pass also reduces
- * the separation diagnostics of the new state in FP64. */
+ * per step on the handle's stream, asynchronously.  The pass of every
+ * diag_every-th step (counted from init) and of the last step of the call
+ * also reduces the separation diagnostics of the new state in FP64 (one
+ * history record each), so lbm_mix_separation after lbm_mix_step always
+ * describes the current state. */
 int lbm_mix_step(lbm_mix* h, long nsteps);
 
 /* Steps in blocks of `check_every` (>= 1) until the steady-state residual
@@ -124,10 +128,11 @@ int lbm_mix_moments_device(lbm_mix* h, double* d_out);
 int lbm_mix_separation(lbm_mix* h, double* CL, double* Cl_tilde, double* mdot_a,
                        double* mdot_b, double* Cl_profile, int* x_min);
 
-/* Copies up to max_records of the most recent per-step diagnostic records,
- * oldest first, into rec[max_records][8] = {step, CL, C~_l, mdot_a, mdot_b,
- * x_min, total mass a, total mass b}; *count gets the number copied.  The
- * library keeps the last 4096 steps.  Synchronises. */
+/* Copies up to max_records of the most recent diagnostic records, oldest
+ * first, into rec[max_records][8] = {record number, CL, C~_l, mdot_a,
+ * mdot_b, x_min, total mass a, total mass b}; *count gets the number copied.
+ * One record per diagnostic step (see lbm_mix_step); the library keeps the
+ * last 4096.  Synchronises. */
 int lbm_mix_history(lbm_mix* h, double* rec, long max_records, long* count);
 
 /* Per-wall-node accommodation coefficients alpha in (0,1] (Eq. A12):

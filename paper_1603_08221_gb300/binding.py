@@ -39,6 +39,7 @@ class lbm_mix_params(ctypes.Structure):
         ("tau_eps", ctypes.c_double),
         ("mu_ratio_a", ctypes.c_double), ("mu_ratio_b", ctypes.c_double),
         ("storage", ctypes.c_int), ("x_periodic", ctypes.c_int),
+        ("diag_every", ctypes.c_int),
     ]
 
 

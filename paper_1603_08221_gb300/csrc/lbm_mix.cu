@@ -143,7 +143,8 @@ __device__ __forceinline__ float psi_dev(float a) {
     q = fmaf(q, a, -1.0f / 3.0f);
     q = fmaf(q, a, 0.5772156649f - 1.5f);
     q = fmaf(q, a, 2.0f);
-    return fmaf(a * a, logf(a), q * a);
+    // __logf: absolute error ~2^-21 on ln a near a = 1, i.e. < 2e-7 in a^2 ln a
+    return fmaf(a * a, __logf(a), q * a);
   }
   if (a >= 15.0f) return 1.0f;
   float num = (((a + 8.5733287401f) * a + 18.0590169730f) * a + 8.6347608925f) * a +
@@ -582,7 +583,9 @@ __device__ __forceinline__ void warp_min(double& v, int& idx) {
 
 // Column sums -> next step's density correction, C_l(x), per-CTA partials;
 // the last CTA to finish reduces the partials in CTA order into one record.
-template <typename ST>
+// DIAG = false: only the column sums (the next step's Eq. rho2 input) are
+// produced; DIAG = true: also C_l(x), the per-strip partials and the record.
+template <bool DIAG, typename ST>
 __device__ __forceinline__ void column_epilogue(const Lat& L, const StepArgs<ST>& a, int x,
                                                 const double acc[4], RedSmem& rs) {
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -603,12 +606,14 @@ __device__ __forceinline__ void column_epilogue(const Lat& L, const StepArgs<ST>
   if (R > 1) {
     // Row-block partials of this strip; the last of its R CTAs to finish
     // adds them in row-block order (independent of arrival order).
-    if (ty == 0 && x < L.Nx) {
+    if (ty == 0) {
+      if (x < L.Nx) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        a.colpart[((size_t)blockIdx.y * 4 + k) * L.Nx + x] = c[k];
+        for (int k = 0; k < 4; ++k)
+          a.colpart[((size_t)blockIdx.y * 4 + k) * L.Nx + x] = c[k];
+      }
+      __threadfence();  // the writers publish before the ticket is taken
     }
-    __threadfence();
     __syncthreads();
     if (tid == 0) {
       unsigned ticket = atomicAdd(a.strip_cnt + blockIdx.x, 1u);
@@ -616,8 +621,8 @@ __device__ __forceinline__ void column_epilogue(const Lat& L, const StepArgs<ST>
     }
     __syncthreads();
     if (!rs.last_strip) return;
-    __threadfence();
     if (ty == 0) {
+      __threadfence();
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         double v = 0.0;
@@ -627,6 +632,13 @@ __device__ __forceinline__ void column_epilogue(const Lat& L, const StepArgs<ST>
       }
       if (tx == 0) a.strip_cnt[blockIdx.x] = 0u;
     }
+  }
+  if (!DIAG) {
+    if (ty == 0 && x < L.Nx) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) a.cs_out[(size_t)k * L.Nx + x] = c[k];
+    }
+    return;
   }
   if (ty == 0) {
     const bool in = interior(L, x);
@@ -730,7 +742,10 @@ __device__ __forceinline__ void column_epilogue(const Lat& L, const StepArgs<ST>
   }
 }
 
-template <typename ST>
+// DIAG: reduce the separation diagnostics of the new state (every
+// diag_every-th step); otherwise only the strips holding the end columns
+// reduce the column sums the next step's density correction needs.
+template <typename ST, bool DIAG>
 __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST> a) {
   __shared__ WallSmem wsm;
   __shared__ RedSmem rsm;
@@ -752,6 +767,7 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
   KahanF acc[4];
   const int j_begin = blockIdx.y * a.rows_per_block;
   const int j_end = min(L.N, j_begin + a.rows_per_block);
+  const bool reduce = DIAG || edge_strip;
   if (in) {
     for (int j = j_begin + ty; j < j_end; j += TY) {
       float fs[2][9];
@@ -770,13 +786,16 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
       for (int sp = 0; sp < 2; ++sp) {
         float mxs = collide(fs[sp], m.rho[sp], L.s[sp], m.ux, m.uy, L.om_e, L.om_eps, om_d,
                             om_q, om_s);
-        acc[sp].add(m.sd[sp]);
-        acc[2 + sp].add(mxs);
+        if (reduce) {
+          acc[sp].add(m.sd[sp]);
+          acc[2 + sp].add(mxs);
+        }
 #pragma unroll
         for (int i = 0; i < 9; ++i) Stor<ST>::st(o + (sp * 9 + i) * TX, fs[sp][i]);
       }
     }
   }
+  if (!reduce) return;  // CTA-uniform
   // column sum of rho_s = N rhobar_s + sum of deviations; the reference part
   // is added once per column (by the ty = 0 thread of the first row block)
   const bool adds_ref = in && ty == 0 && blockIdx.y == 0;
@@ -786,7 +805,7 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
     accd[sp] = (adds_ref ? (double)L.N * (double)C.rb[sp] : 0.0) + acc[sp].value();
   accd[2] = acc[2].value();
   accd[3] = acc[3].value();
-  column_epilogue(L, a, x, accd, rsm);
+  column_epilogue<DIAG>(L, a, x, accd, rsm);
 }
 
 // ---------------------------------------------------------- moments kernel
@@ -1014,6 +1033,7 @@ int validate(const lbm_mix_params* p, int* Nx_out) {
     return set_err(LBM_EINVAL, "viscosity ratios must be > 0");
   if (p->storage != LBM_FP32) return set_err(LBM_EINVAL, "storage must be LBM_FP32");
   if (p->x_periodic != 0 && p->x_periodic != 1) return set_err(LBM_EINVAL, "x_periodic is 0 or 1");
+  if (p->diag_every < 1) return set_err(LBM_EINVAL, "diag_every must be >= 1");
   long pitch = (Nx + 31) / 32 * 32;
   double elems = 18.0 * (double)p->N * (double)pitch;
   if (elems >= 2147483648.0)
@@ -1087,7 +1107,7 @@ int reset_diag(lbm_mix* h) {
   return LBM_OK;
 }
 
-int launch_step(lbm_mix* h) {
+int launch_step(lbm_mix* h, bool diag) {
   StepArgs<float> a;
   const int b = h->cur;
   a.fin = h->buf[b];
@@ -1105,7 +1125,10 @@ int launch_step(lbm_mix* h) {
   a.strip_cnt = h->strip_cnt;
   a.rows_per_block = h->rows_per_block;
   dim3 blk(TX, TY), grd(h->nblocks, h->R);
-  lbm_step_kernel<float><<<grd, blk, 0, h->stream>>>(h->L, a);
+  if (diag)
+    lbm_step_kernel<float, true><<<grd, blk, 0, h->stream>>>(h->L, a);
+  else
+    lbm_step_kernel<float, false><<<grd, blk, 0, h->stream>>>(h->L, a);
   CK(cudaGetLastError());
   h->cur = 1 - b;
   h->steps++;
@@ -1225,6 +1248,7 @@ void lbm_mix_default_params(lbm_mix_params* p) {
   p->mu_ratio_b = 1.0;
   p->storage = LBM_FP32;
   p->x_periodic = 0;
+  p->diag_every = 1;
 }
 
 const char* lbm_mix_strerror(int s) {
@@ -1393,8 +1417,11 @@ int lbm_mix_step(lbm_mix* h, long nsteps) {
   int st = check_handle(h);
   if (st) return st;
   if (nsteps < 0) return set_err(LBM_EINVAL, "nsteps < 0");
-  for (long t = 0; t < nsteps; ++t)
-    if ((st = launch_step(h))) return st;
+  // diagnostics on every diag_every-th step and on the last step of the call
+  for (long t = 0; t < nsteps; ++t) {
+    const bool diag = (t == nsteps - 1) || ((h->steps + 1) % h->p.diag_every == 0);
+    if ((st = launch_step(h, diag))) return st;
+  }
   return LBM_OK;
 }
 
@@ -1625,7 +1652,7 @@ int lbm_mix_step_noalloc(const lbm_mix_params* p, const float* d_in, float* d_ou
   a.colpart = nullptr;  // one row block per strip: no row-block partials
   a.rows_per_block = (L.N + TY - 1) / TY * TY;
   dim3 blk(TX, TY), grd(nstrips, 1);
-  lbm_step_kernel<float><<<grd, blk, 0, s>>>(L, a);
+  lbm_step_kernel<float, true><<<grd, blk, 0, s>>>(L, a);
   CK(cudaGetLastError());
   return LBM_OK;
 }

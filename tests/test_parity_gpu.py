@@ -194,6 +194,25 @@ def test_history_matches_oracle_separation():
     assert np.abs(got - np.array(cl)).max() < 1e-6 + 1e-3 * np.abs(cl).max()
 
 
+def test_diag_every_changes_only_the_records():
+    """Diagnostic reductions every 7th step (and at the end of each call):
+    the populations are bitwise those of the every-step run and the records
+    of the diagnostic steps agree."""
+    p = workloads.preset("neon_argon_2048x32", N=20, N_x=100, theta=1.5)
+    g1 = binding.LbmMix(**p)
+    g7 = binding.LbmMix(diag_every=7, **p)
+    for g in (g1, g7):
+        g.init()
+        g.step(30)
+        g.step(5)
+    assert np.array_equal(g1.get_post_state(), g7.get_post_state())
+    h1, h7 = g1.history(), g7.history()
+    assert len(h1) == 35 and len(h7) == 6  # steps 7, 14, 21, 28, 30 (end of call), 35
+    s1, s7 = g1.separation(), g7.separation()
+    assert all(np.array_equal(s1[k], s7[k]) for k in s1)
+    assert np.array_equal(h1[-1, 1:], h7[-1, 1:])
+
+
 def test_moments_device_matches_host():
     torch = pytest.importorskip("torch")
     p = workloads.preset("heli_argon_320x16", N=8, N_x=40)
