@@ -74,6 +74,9 @@ struct Lat {
   float s[2];            // s_sigma = m_min / m_sigma
   float cw0[2];          // rest-equilibrium weights w_i alpha_si: rest (9 - 5s)/9,
   float cw1[2], cw5[2];  // axis s/9, diagonal s/36
+  // coefficients of the non-equilibrium energy moments on the deviations
+  // (rest, axis, diagonal): e: -2s, 3 - 2s, 6 - 2s; eps: 3s, 3s - 6, 3s - 3
+  float ke[2][3], kp[2][3];
   float inv_c_lam;       // 1 / (3 mu sqrt(pi/6))
   float c_lam;           // 3 mu sqrt(pi/6): lambda = c_lam / (n sqrt(m_x))
   float c_xl[2];         // 3 mu_s sqrt(pi/(6 m_s)): x_s lambda_s = c_xl / n
@@ -406,17 +409,18 @@ __device__ __forceinline__ float dbb_r(const Lat& L, const ColRef& C, const ST* 
 // 1/6, 1/12, 1/4, 1/4), m^eq = rho_s (1, -4 + 2s + 3u^2, 4 - 3s - 3u^2, u_x,
 // -u_x, u_y, -u_y, u_x^2 - u_y^2, u_x u_y).  The reference has m = m^eq(u=0),
 // so e - e^eq = sum_i (e_i + 4 - 2s) g_i - 3 rho u^2 and
-// eps - eps^eq = sum_i (eps_i - 4 + 3s) g_i + 3 rho u^2 need no large terms.
+// eps - eps^eq = sum_i (eps_i - 4 + 3s) g_i + 3 rho u^2 need no large terms
+// (ke, kp hold those coefficients for the rest, axis and diagonal classes).
 // Returns the x component of the species momentum of Eq. rhou,
 // j_x - (j_x - rho_s u_x)/(2 tau_d).
-__device__ __forceinline__ float collide(float g[9], float rho, float s, float ux, float uy,
-                                         float om_e, float om_eps, float om_d, float om_q,
-                                         float om_s) {
+__device__ __forceinline__ float collide(float g[9], float rho, const float ke[3],
+                                         const float kp[3], float ux, float uy, float om_e,
+                                         float om_eps, float om_d, float om_q, float om_s) {
   const float ru2 = 3.0f * rho * (ux * ux + uy * uy);
   const float a14 = (g[1] + g[2]) + (g[3] + g[4]);
   const float a58 = (g[5] + g[6]) + (g[7] + g[8]);
-  const float ne = fmaf(-2.0f * s, g[0], fmaf(3.0f - 2.0f * s, a14, fmaf(6.0f - 2.0f * s, a58, -ru2)));
-  const float neps = fmaf(3.0f * s, g[0], fmaf(3.0f * s - 6.0f, a14, fmaf(3.0f * s - 3.0f, a58, ru2)));
+  const float ne = fmaf(ke[0], g[0], fmaf(ke[1], a14, fmaf(ke[2], a58, -ru2)));
+  const float neps = fmaf(kp[0], g[0], fmaf(kp[1], a14, fmaf(kp[2], a58, ru2)));
   const float dx56 = (g[5] - g[6]) + (g[8] - g[7]);
   const float dy56 = (g[5] - g[7]) + (g[6] - g[8]);
   const float jx = (g[1] - g[3]) + dx56;
@@ -784,8 +788,8 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
       ST* o = a.fout + base + j * RS;
 #pragma unroll
       for (int sp = 0; sp < 2; ++sp) {
-        float mxs = collide(fs[sp], m.rho[sp], L.s[sp], m.ux, m.uy, L.om_e, L.om_eps, om_d,
-                            om_q, om_s);
+        float mxs = collide(fs[sp], m.rho[sp], L.ke[sp], L.kp[sp], m.ux, m.uy, L.om_e, L.om_eps,
+                            om_d, om_q, om_s);
         if (reduce) {
           acc[sp].add(m.sd[sp]);
           acc[2 + sp].add(mxs);
@@ -1074,6 +1078,13 @@ Lat derive(const lbm_mix_params* p, int Nx) {
     L.cw0[sp] = (float)((9.0 - 5.0 * (double)L.s[sp]) / 9.0);
     L.cw1[sp] = (float)((double)L.s[sp] / 9.0);
     L.cw5[sp] = (float)((double)L.s[sp] / 36.0);
+    const float sf = L.s[sp];
+    L.ke[sp][0] = -2.0f * sf;
+    L.ke[sp][1] = 3.0f - 2.0f * sf;
+    L.ke[sp][2] = 6.0f - 2.0f * sf;
+    L.kp[sp][0] = 3.0f * sf;
+    L.kp[sp][1] = 3.0f * sf - 6.0f;
+    L.kp[sp][2] = 3.0f * sf - 3.0f;
     L.mh[sp] = mh[sp];
     double cxl = 3.0 * mu_s[sp] * sqrt(PI / (6.0 * mh[sp]));
     L.c_xl[sp] = (float)cxl;
