@@ -42,7 +42,11 @@ extern "C" {
 #define LBM_ENOTCONVERGED (-5)  /* run_to_steady hit max_steps */
 #define LBM_ETIMEOUT (-6)       /* reserved: a bounded device wait expired */
 
-#define LBM_FP32 0 /* population storage: FP32 */
+/* Population storage.  Every form stores deviations from the rest
+ * equilibrium of a per-column reference density and computes in FP32. */
+#define LBM_FP32 0 /* FP32 deviations (144 B per node per step) */
+#define LBM_BF16 1 /* BF16 deviations (72 B per node per step) */
+#define LBM_FP16 2 /* FP16 deviations (72 B per node per step) */
 
 typedef struct lbm_mix lbm_mix; /* opaque, owned by the library */
 
@@ -61,7 +65,7 @@ typedef struct {
                            scaled by (2 - alpha)/alpha per wall node */
   double tau_rho, tau_e, tau_eps; /* fixed relaxation times (Sec. 3.3) */
   double mu_ratio_a, mu_ratio_b;  /* mu_sigma / mu of the mixture */
-  int storage;          /* LBM_FP32 */
+  int storage;          /* LBM_FP32, LBM_BF16 or LBM_FP16 */
   int x_periodic;       /* 1: periodic in x instead of pressure ends */
   int diag_every;       /* >= 1: steps between separation-diagnostic reductions */
 } lbm_mix_params;

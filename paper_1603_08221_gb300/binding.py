@@ -25,6 +25,8 @@ LBM_ENONFINITE = -4
 LBM_ENOTCONVERGED = -5
 LBM_ETIMEOUT = -6
 LBM_FP32 = 0
+LBM_BF16 = 1
+LBM_FP16 = 2
 
 
 class lbm_mix_params(ctypes.Structure):

@@ -22,6 +22,8 @@
 // strip over ALL rows, sweeping rows in steps of TY, so that every per-column
 // quantity (the tau_q of the two walls, the column sums) is produced inside
 // one CTA without atomics and in a fixed order.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -77,6 +79,9 @@ struct Lat {
   // coefficients of the non-equilibrium energy moments on the deviations
   // (rest, axis, diagonal): e: -2s, 3 - 2s, 6 - 2s; eps: 3s, 3s - 6, 3s - 3
   float ke[2][3], kp[2][3];
+  // the same per-species constants as (species a, species b) pairs for the
+  // packed FP32x2 arithmetic
+  float2 s2, cw1_2, cw5_2, c_xl2, inv_c_xl2, ke2[3], kp2[3];
   float inv_c_lam;       // 1 / (3 mu sqrt(pi/6))
   float c_lam;           // 3 mu sqrt(pi/6): lambda = c_lam / (n sqrt(m_x))
   float c_xl[2];         // 3 mu_s sqrt(pi/(6 m_s)): x_s lambda_s = c_xl / n
@@ -166,6 +171,52 @@ __device__ __forceinline__ float dpsi_dev(float a) {
   return 2.0f * expf(-a) * (1.0f - xexe1_rational(a));
 }
 
+// ------------------------------------------------- packed FP32x2 helpers
+// The two species run the same arithmetic on different data; Blackwell's
+// packed FP32x2 instructions do both in one issue slot.  Each component is
+// rounded exactly as the scalar operation would be.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, f2(-1.0f), a);  // exact: a - b with one rounding
+}
+
+// psi at two arguments at once without branches: both formulas of psi_dev
+// are evaluated (on min(a, 1) and max(a, 1)) and the right one selected.
+__device__ __forceinline__ float2 psi2(float2 a) {
+  const float2 as = make_float2(fminf(a.x, 1.0f), fminf(a.y, 1.0f));
+  float2 q = f2(-1.0f / 179625600.0f);
+  q = fma2(q, as, f2(1.0f / 14515200.0f));
+  q = fma2(q, as, f2(-1.0f / 1270080.0f));
+  q = fma2(q, as, f2(1.0f / 120960.0f));
+  q = fma2(q, as, f2(-1.0f / 12600.0f));
+  q = fma2(q, as, f2(1.0f / 1440.0f));
+  q = fma2(q, as, f2(-1.0f / 180.0f));
+  q = fma2(q, as, f2(1.0f / 24.0f));
+  q = fma2(q, as, f2(-1.0f / 3.0f));
+  q = fma2(q, as, f2(0.5772156649f - 1.5f));
+  q = fma2(q, as, f2(2.0f));
+  const float2 lg = make_float2(__logf(as.x), __logf(as.y));
+  const float2 ps = fma2(mul2(as, as), lg, mul2(q, as));
+  const float2 al = make_float2(fmaxf(a.x, 1.0f), fmaxf(a.y, 1.0f));
+  float2 num = add2(al, f2(8.5733287401f));
+  num = fma2(num, al, f2(18.0590169730f));
+  num = fma2(num, al, f2(8.6347608925f));
+  num = fma2(num, al, f2(0.2677737343f));
+  float2 den = add2(al, f2(9.5733223454f));
+  den = fma2(den, al, f2(25.6329561486f));
+  den = fma2(den, al, f2(21.0996530827f));
+  den = fma2(den, al, f2(3.9584969228f));
+  const float2 R = make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+  const float2 e = make_float2(__expf(-al.x), __expf(-al.y));
+  // 1 + e^{-a} [(a - 1) - a R]
+  const float2 pl = fma2(e, fma2(make_float2(-al.x, -al.y), R, add2(al, f2(-1.0f))), f2(1.0f));
+  return make_float2(a.x <= 1.0f ? (a.x > 0.0f ? ps.x : 0.0f) : pl.x,
+                     a.y <= 1.0f ? (a.y > 0.0f ? ps.y : 0.0f) : pl.y);
+}
+
 // ------------------------------------------------------------- storage
 // Populations are stored as deviations d_i = f_i - w_i alpha_si rhobar_s(x)
 // from the rest equilibrium (Eq. feq with u = 0) of a fixed per-column
@@ -180,6 +231,22 @@ template <>
 struct Stor<float> {
   static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
   static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+// Reduced-precision storage of the same deviations: loads widen to FP32, all
+// arithmetic is FP32, stores round to nearest.
+template <>
+struct Stor<__nv_bfloat16> {
+  static __device__ __forceinline__ float ld(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldg(p));
+  }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) {
+    *p = __float2bfloat16_rn(v);
+  }
+};
+template <>
+struct Stor<__half> {
+  static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+  static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 };
 
 struct Ends {
@@ -341,32 +408,116 @@ __device__ __forceinline__ void macro(const Lat& L, const ColRef& C, const float
   m.mx = rho * m.inv_n;  // m_x = rho / n
 }
 
-// Wall-confinement factor Psi(y) = (psi(y/lambda) + psi((H-y)/lambda))/2.
-__device__ __forceinline__ float Psi_dev(float y, float H, float inv_lam) {
-  return 0.5f * (psi_dev(y * inv_lam) + psi_dev((H - y) * inv_lam));
+// ------------------------------------------- packed per-node arithmetic
+// The node update of the step and moments kernels works on g[i] =
+// (species a, species b) pairs of the pre-collision deviations.
+struct Macro2 {
+  float2 sd;   // sum of deviations: rho_s - rhobar_s
+  float2 rho;  // species densities
+  float2 jx, jy;
+  float ux, uy;
+  float n, inv_n, mx;
+};
+
+__device__ __forceinline__ void macro2(const Lat& L, const ColRef& C, const float2 g[9],
+                                       Macro2& m) {
+  m.sd = add2(add2(add2(add2(g[0], g[1]), add2(g[2], g[3])), add2(add2(g[4], g[5]), add2(g[6], g[7]))),
+              g[8]);
+  m.rho = add2(make_float2(C.rb[0], C.rb[1]), m.sd);
+  m.jx = add2(add2(sub2(g[1], g[3]), sub2(g[5], g[6])), sub2(g[8], g[7]));
+  m.jy = add2(add2(sub2(g[2], g[4]), sub2(g[5], g[7])), sub2(g[6], g[8]));
+  const float rho = m.rho.x + m.rho.y;
+  const float inv_rho = __fdividef(1.0f, rho);
+  m.ux = (m.jx.x + m.jx.y) * inv_rho;
+  m.uy = (m.jy.x + m.jy.y) * inv_rho;
+  m.n = fmaf(m.rho.x, L.s[0], m.rho.y * L.s[1]);  // number density (Eq. P)
+  m.inv_n = __fdividef(1.0f, m.n);
+  m.mx = rho * m.inv_n;  // m_x = rho / n
 }
 
-// Relaxation rates 1/tau_s (Eq. taos) and 1/tau_d (Eq. EQFrsp with
-// lambda_se = lambda_s Psi(y; lambda_s), lambda_s = (mu_s/p_s)
-// sqrt(pi k_B T/(2 m_s)), p_s = x_s p).
-__device__ __forceinline__ void rates(const Lat& L, const Macro& m, float y, float& om_s,
-                                      float& om_d) {
-  float rs_mx = rsqrtf(m.mx);
-  float lam = L.c_lam * m.inv_n * rs_mx;                // mixture mean free path
-  float inv_lam = L.inv_c_lam * m.n * (m.mx * rs_mx);  // 1 / lambda
-  float ts = lam * Psi_dev(y, L.H, inv_lam) * L.c_ts * rs_mx;  // tau_s - 1/2
+// 1/tau_s (Eq. taos) and 1/tau_d (Eq. EQFrsp with lambda_se = lambda_s
+// Psi(y; lambda_s), lambda_s = (mu_s/p_s) sqrt(pi k_B T/(2 m_s)), p_s = x_s p),
+// with the wall-confinement factor Psi(y) = (psi(y/lambda) + psi((H-y)/lambda))/2
+// of the effective mean free path; the six psi values come from three packed
+// evaluations.
+__device__ __forceinline__ void rates2(const Lat& L, const Macro2& m, float y, float& om_s,
+                                       float& om_d) {
+  const float rs_mx = rsqrtf(m.mx);
+  const float lam = L.c_lam * m.inv_n * rs_mx;                // mixture mean free path
+  const float inv_lam = L.inv_c_lam * m.n * (m.mx * rs_mx);  // 1 / lambda
+  const float2 yy = make_float2(y, L.H - y);
+  const float2 inv_ls = mul2(mul2(m.rho, L.s2), L.inv_c_xl2);  // 1 / lambda_s
+  const float2 pm = psi2(mul2(yy, f2(inv_lam)));
+  const float2 pa = psi2(mul2(yy, f2(inv_ls.x)));
+  const float2 pb = psi2(mul2(yy, f2(inv_ls.y)));
+  const float ts = lam * (0.5f * (pm.x + pm.y)) * L.c_ts * rs_mx;  // tau_s - 1/2
   om_s = __fdividef(1.0f, 0.5f + ts);
-  float br = 0.0f;
-#pragma unroll
-  for (int sp = 0; sp < 2; ++sp) {
-    float n_s = m.rho[sp] * L.s[sp];
-    float inv_lam_s = n_s * L.inv_c_xl[sp];                          // 1 / lambda_s
-    float xl_e = L.c_xl[sp] * m.inv_n * Psi_dev(y, L.H, inv_lam_s);  // x_s lambda_se
-    br += rsqrtf(xl_e);
-  }
+  // x_s lambda_se = c_xl / n * Psi(y; lambda_s)
+  const float2 xle = mul2(mul2(L.c_xl2, f2(0.5f * m.inv_n)),
+                          make_float2(pa.x + pa.y, pb.x + pb.y));
+  const float br = rsqrtf(xle.x) + rsqrtf(xle.y);
   // tau_d = 1/2 + c_td / (m_x br^2)  =>  1/tau_d = d / (d/2 + c_td), d = m_x br^2
-  float d = m.mx * br * br;
+  const float d = m.mx * br * br;
   om_d = __fdividef(d, fmaf(0.5f, d, L.c_td));
+}
+
+// MRT collision of both species at once (Eqs. MR, S, feq) on the deviations g from
+// the rest equilibrium of the column reference, in moment space:
+// f' = f - M^{-1} S (m - m^eq), M^{-1} = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12,
+// 1/6, 1/12, 1/4, 1/4), m^eq = rho_s (1, -4 + 2s + 3u^2, 4 - 3s - 3u^2, u_x,
+// -u_x, u_y, -u_y, u_x^2 - u_y^2, u_x u_y).  The reference has m = m^eq(u=0),
+// so e - e^eq = sum_i (e_i + 4 - 2s) g_i - 3 rho u^2 and
+// eps - eps^eq = sum_i (eps_i - 4 + 3s) g_i + 3 rho u^2 need no large terms
+// (ke, kp hold those coefficients for the rest, axis and diagonal classes).
+// Returns the x components of the species momenta of Eq. rhou,
+// j_x - (j_x - rho_s u_x)/(2 tau_d).
+__device__ __forceinline__ float2 collide2(float2 g[9], const Lat& L, float2 rho, float ux,
+                                           float uy, float om_e, float om_eps, float om_d,
+                                           float om_q, float om_s) {
+  const float2 ru2 = mul2(f2(3.0f * (ux * ux + uy * uy)), rho);
+  const float2 a14 = add2(add2(g[1], g[2]), add2(g[3], g[4]));
+  const float2 a58 = add2(add2(g[5], g[6]), add2(g[7], g[8]));
+  const float2 ne =
+      fma2(L.ke2[0], g[0], fma2(L.ke2[1], a14, fma2(L.ke2[2], a58, make_float2(-ru2.x, -ru2.y))));
+  const float2 neps = fma2(L.kp2[0], g[0], fma2(L.kp2[1], a14, fma2(L.kp2[2], a58, ru2)));
+  const float2 d13 = sub2(g[1], g[3]), d24 = sub2(g[2], g[4]);
+  const float2 dx56 = add2(sub2(g[5], g[6]), sub2(g[8], g[7]));
+  const float2 dy56 = add2(sub2(g[5], g[7]), sub2(g[6], g[8]));
+  const float2 jx = add2(d13, dx56);
+  const float2 jy = add2(d24, dy56);
+  const float2 qx = fma2(f2(-2.0f), d13, dx56);
+  const float2 qy = fma2(f2(-2.0f), d24, dy56);
+  const float2 pxx = sub2(add2(g[1], g[3]), add2(g[2], g[4]));
+  const float2 pxy = sub2(add2(g[5], g[7]), add2(g[6], g[8]));
+  const float2 de = mul2(f2(om_e), ne);
+  const float2 deps = mul2(f2(om_eps), neps);
+  const float2 djx = mul2(f2(om_d), fma2(rho, f2(-ux), jx));
+  const float2 djy = mul2(f2(om_d), fma2(rho, f2(-uy), jy));
+  const float2 dqx = mul2(f2(om_q), fma2(rho, f2(ux), qx));
+  const float2 dqy = mul2(f2(om_q), fma2(rho, f2(uy), qy));
+  const float2 dpxx = mul2(f2(om_s), fma2(rho, f2(-(ux * ux - uy * uy)), pxx));
+  const float2 dpxy = mul2(f2(om_s), fma2(rho, f2(-(ux * uy)), pxy));
+  const float2 c0 = mul2(sub2(de, deps), f2(1.0f / 9.0f));
+  const float2 c14 = fma2(de, f2(1.0f / 36.0f), mul2(deps, f2(1.0f / 18.0f)));
+  const float2 c58 = fma2(de, f2(-1.0f / 18.0f), mul2(deps, f2(-1.0f / 36.0f)));
+  const float2 ax = mul2(sub2(dqx, djx), f2(1.0f / 6.0f));
+  const float2 ay = mul2(sub2(dqy, djy), f2(1.0f / 6.0f));
+  const float2 bx = fma2(djx, f2(-1.0f / 6.0f), mul2(dqx, f2(-1.0f / 12.0f)));
+  const float2 by = fma2(djy, f2(-1.0f / 6.0f), mul2(dqy, f2(-1.0f / 12.0f)));
+  const float2 pp = mul2(dpxx, f2(0.25f)), pq = mul2(dpxy, f2(0.25f));
+  const float2 u1 = sub2(c14, pp), u2 = add2(c14, pp);  // shared by opposite axis pairs
+  const float2 v5 = sub2(c58, pq), v6 = add2(c58, pq);  // and by opposite diagonal pairs
+  const float2 w5 = add2(bx, by), w6 = sub2(by, bx);
+  g[0] = add2(g[0], c0);
+  g[1] = add2(g[1], add2(u1, ax));
+  g[3] = add2(g[3], sub2(u1, ax));
+  g[2] = add2(g[2], add2(u2, ay));
+  g[4] = add2(g[4], sub2(u2, ay));
+  g[5] = add2(g[5], add2(v5, w5));
+  g[7] = add2(g[7], sub2(v5, w5));
+  g[6] = add2(g[6], add2(v6, w6));
+  g[8] = add2(g[8], sub2(v6, w6));
+  return fma2(f2(-0.5f), djx, jx);
 }
 
 // tau_q of Eq. taoq from the wall node's lambda and m_x (tau'_s(0) in its
@@ -401,59 +552,6 @@ __device__ __forceinline__ float dbb_r(const Lat& L, const ColRef& C, const ST* 
   float mx = (rho[0] + rho[1]) / fmaf(rho[0], L.s[0], rho[1] * L.s[1]);
   float cm = L.c_m0 * (2.0f - alpha) / alpha;
   return 2.0f - 2.0f / (1.0f + cm * sqrtf(kPi * mx / 6.0f));
-}
-
-// MRT collision of one species (Eqs. MR, S, feq) on the deviations g from
-// the rest equilibrium of the column reference, in moment space:
-// f' = f - M^{-1} S (m - m^eq), M^{-1} = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12,
-// 1/6, 1/12, 1/4, 1/4), m^eq = rho_s (1, -4 + 2s + 3u^2, 4 - 3s - 3u^2, u_x,
-// -u_x, u_y, -u_y, u_x^2 - u_y^2, u_x u_y).  The reference has m = m^eq(u=0),
-// so e - e^eq = sum_i (e_i + 4 - 2s) g_i - 3 rho u^2 and
-// eps - eps^eq = sum_i (eps_i - 4 + 3s) g_i + 3 rho u^2 need no large terms
-// (ke, kp hold those coefficients for the rest, axis and diagonal classes).
-// Returns the x component of the species momentum of Eq. rhou,
-// j_x - (j_x - rho_s u_x)/(2 tau_d).
-__device__ __forceinline__ float collide(float g[9], float rho, const float ke[3],
-                                         const float kp[3], float ux, float uy, float om_e,
-                                         float om_eps, float om_d, float om_q, float om_s) {
-  const float ru2 = 3.0f * rho * (ux * ux + uy * uy);
-  const float a14 = (g[1] + g[2]) + (g[3] + g[4]);
-  const float a58 = (g[5] + g[6]) + (g[7] + g[8]);
-  const float ne = fmaf(ke[0], g[0], fmaf(ke[1], a14, fmaf(ke[2], a58, -ru2)));
-  const float neps = fmaf(kp[0], g[0], fmaf(kp[1], a14, fmaf(kp[2], a58, ru2)));
-  const float dx56 = (g[5] - g[6]) + (g[8] - g[7]);
-  const float dy56 = (g[5] - g[7]) + (g[6] - g[8]);
-  const float jx = (g[1] - g[3]) + dx56;
-  const float jy = (g[2] - g[4]) + dy56;
-  const float qx = fmaf(2.0f, g[3] - g[1], dx56);
-  const float qy = fmaf(2.0f, g[4] - g[2], dy56);
-  const float pxx = (g[1] + g[3]) - (g[2] + g[4]);
-  const float pxy = (g[5] + g[7]) - (g[6] + g[8]);
-  const float de = om_e * ne;
-  const float deps = om_eps * neps;
-  const float djx = om_d * fmaf(-rho, ux, jx);
-  const float djy = om_d * fmaf(-rho, uy, jy);
-  const float dqx = om_q * fmaf(rho, ux, qx);
-  const float dqy = om_q * fmaf(rho, uy, qy);
-  const float dpxx = om_s * fmaf(-rho, ux * ux - uy * uy, pxx);
-  const float dpxy = om_s * fmaf(-rho, ux * uy, pxy);
-  const float c0 = (de - deps) * (1.0f / 9.0f);
-  const float c14 = de * (1.0f / 36.0f) + deps * (1.0f / 18.0f);
-  const float c58 = -(de * (1.0f / 18.0f) + deps * (1.0f / 36.0f));
-  const float ax = (dqx - djx) * (1.0f / 6.0f), ay = (dqy - djy) * (1.0f / 6.0f);
-  const float bx = -(djx * (1.0f / 6.0f) + dqx * (1.0f / 12.0f));
-  const float by = -(djy * (1.0f / 6.0f) + dqy * (1.0f / 12.0f));
-  const float pp = dpxx * 0.25f, pq = dpxy * 0.25f;
-  g[0] += c0;
-  g[1] += c14 + ax - pp;
-  g[2] += c14 + ay + pp;
-  g[3] += c14 - ax - pp;
-  g[4] += c14 - ay + pp;
-  g[5] += c58 + bx + by - pq;
-  g[6] += c58 - bx + by + pq;
-  g[7] += c58 - bx - by - pq;
-  g[8] += c58 + bx - by + pq;
-  return jx - 0.5f * djx;
 }
 
 // Density-correction factors of Eq. rho2 for the ghost columns, from the
@@ -780,22 +878,27 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
         pull_fast(p, p + offl, p + offr, L, C, fs);
       else
         pull_node(a.fin, L, E, C, x, j, r_bot, r_top, fs);
-      Macro m;
-      macro(L, C, fs, m);
+      float2 g[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) g[i] = make_float2(fs[0][i], fs[1][i]);
+      Macro2 m;
+      macro2(L, C, g, m);
       float om_s, om_d;
-      rates(L, m, (float)j + 0.5f, om_s, om_d);
+      rates2(L, m, (float)j + 0.5f, om_s, om_d);
       const float om_q = wsm.om_q[j < half ? 0 : 1][tx];
+      const float2 mxs =
+          collide2(g, L, m.rho, m.ux, m.uy, L.om_e, L.om_eps, om_d, om_q, om_s);
+      if (reduce) {
+        acc[0].add(m.sd.x);
+        acc[1].add(m.sd.y);
+        acc[2].add(mxs.x);
+        acc[3].add(mxs.y);
+      }
       ST* o = a.fout + base + j * RS;
 #pragma unroll
-      for (int sp = 0; sp < 2; ++sp) {
-        float mxs = collide(fs[sp], m.rho[sp], L.ke[sp], L.kp[sp], m.ux, m.uy, L.om_e, L.om_eps,
-                            om_d, om_q, om_s);
-        if (reduce) {
-          acc[sp].add(m.sd[sp]);
-          acc[2 + sp].add(mxs);
-        }
-#pragma unroll
-        for (int i = 0; i < 9; ++i) Stor<ST>::st(o + (sp * 9 + i) * TX, fs[sp][i]);
+      for (int i = 0; i < 9; ++i) {
+        Stor<ST>::st(o + i * TX, g[i].x);
+        Stor<ST>::st(o + (9 + i) * TX, g[i].y);
       }
     }
   }
@@ -839,20 +942,25 @@ __global__ void __launch_bounds__(TX* TY)
     } else {
       pull_node(fin, L, E, C, x, j, wsm.r[0][tx], wsm.r[1][tx], fs);
     }
-    Macro m;
-    macro(L, C, fs, m);
+    float2 g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = make_float2(fs[0][i], fs[1][i]);
+    Macro2 m;
+    macro2(L, C, g, m);
     float om_s, om_d;
-    rates(L, m, (float)j + 0.5f, om_s, om_d);
+    rates2(L, m, (float)j + 0.5f, om_s, om_d);
     // Eq. rhou: (2 tau_d - 1)/(2 tau_d) = 1 - om_d/2, 1/(2 tau_d) = om_d/2
     const float w1 = 1.0f - 0.5f * om_d, w2 = 0.5f * om_d;
     const size_t o = (size_t)j * L.Nx + x;
+    const float rho_s[2] = {m.rho.x, m.rho.y}, sd[2] = {m.sd.x, m.sd.y};
+    const float jxs[2] = {m.jx.x, m.jx.y}, jys[2] = {m.jy.x, m.jy.y};
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp) {
-      float mx = fmaf(w1, m.jx[sp], w2 * m.rho[sp] * m.ux);
-      float my = fmaf(w1, m.jy[sp], w2 * m.rho[sp] * m.uy);
-      out[sp * plane + o] = (double)C.rb[sp] + (double)m.sd[sp];
-      out[(2 + 2 * sp) * plane + o] = (double)(mx / m.rho[sp]);
-      out[(3 + 2 * sp) * plane + o] = (double)(my / m.rho[sp]);
+      float mx = fmaf(w1, jxs[sp], w2 * rho_s[sp] * m.ux);
+      float my = fmaf(w1, jys[sp], w2 * rho_s[sp] * m.uy);
+      out[sp * plane + o] = (double)C.rb[sp] + (double)sd[sp];
+      out[(2 + 2 * sp) * plane + o] = (double)(mx / rho_s[sp]);
+      out[(3 + 2 * sp) * plane + o] = (double)(my / rho_s[sp]);
     }
   }
 }
@@ -987,7 +1095,8 @@ struct lbm_mix {
   cudaStream_t stream;
   bool own_stream;
   int nblocks;
-  float* buf[2];      // post-collision deviations, A/B
+  void* buf[2];       // post-collision deviations, A/B (element type per storage)
+  size_t elem;        // bytes per stored population
   float* refrho;      // [2][Nx] reference densities rhobar_s(x)
   float* scratch;     // full-population staging for get_post_state (lazy)
   double* cs[2];
@@ -1035,7 +1144,8 @@ int validate(const lbm_mix_params* p, int* Nx_out) {
     return set_err(LBM_EINVAL, "tau_rho, tau_e, tau_eps must exceed 1/2");
   if (!(p->mu_ratio_a > 0 && p->mu_ratio_b > 0))
     return set_err(LBM_EINVAL, "viscosity ratios must be > 0");
-  if (p->storage != LBM_FP32) return set_err(LBM_EINVAL, "storage must be LBM_FP32");
+  if (p->storage != LBM_FP32 && p->storage != LBM_BF16 && p->storage != LBM_FP16)
+    return set_err(LBM_EINVAL, "storage must be LBM_FP32, LBM_BF16 or LBM_FP16");
   if (p->x_periodic != 0 && p->x_periodic != 1) return set_err(LBM_EINVAL, "x_periodic is 0 or 1");
   if (p->diag_every < 1) return set_err(LBM_EINVAL, "diag_every must be >= 1");
   long pitch = (Nx + 31) / 32 * 32;
@@ -1085,10 +1195,22 @@ Lat derive(const lbm_mix_params* p, int Nx) {
     L.kp[sp][0] = 3.0f * sf;
     L.kp[sp][1] = 3.0f * sf - 6.0f;
     L.kp[sp][2] = 3.0f * sf - 3.0f;
+  }
+  for (int sp = 0; sp < 2; ++sp) {
+    float* s2 = &L.s2.x;
+    s2[sp] = L.s[sp];
+    (&L.cw1_2.x)[sp] = L.cw1[sp];
+    (&L.cw5_2.x)[sp] = L.cw5[sp];
+    for (int k = 0; k < 3; ++k) {
+      (&L.ke2[k].x)[sp] = L.ke[sp][k];
+      (&L.kp2[k].x)[sp] = L.kp[sp][k];
+    }
     L.mh[sp] = mh[sp];
     double cxl = 3.0 * mu_s[sp] * sqrt(PI / (6.0 * mh[sp]));
     L.c_xl[sp] = (float)cxl;
     L.inv_c_xl[sp] = (float)(1.0 / cxl);
+    (&L.c_xl2.x)[sp] = L.c_xl[sp];
+    (&L.inv_c_xl2.x)[sp] = L.inv_c_xl[sp];
     L.rho_in[sp] = p->theta * Ci[sp] * mh[sp];
     L.rho_out[sp] = Co[sp] * mh[sp];
   }
@@ -1104,11 +1226,26 @@ Lat derive(const lbm_mix_params* p, int Nx) {
   return L;
 }
 
+// Calls f(type tag) with the storage element type of the handle.
+template <typename F>
+int with_storage(const lbm_mix* h, F&& f) {
+  switch (h->p.storage) {
+    case LBM_FP32: return f(float());
+    case LBM_BF16: return f(__nv_bfloat16());
+    case LBM_FP16: return f(__half());
+    default: return set_err(LBM_EINVAL, "unknown storage %d", h->p.storage);
+  }
+}
+
 int launch_colsum(lbm_mix* h, int b) {
-  dim3 blk(128), grd((h->L.Nx + 127) / 128);
-  lbm_colsum_kernel<float><<<grd, blk, 0, h->stream>>>(h->L, h->buf[b], h->refrho, h->cs[b]);
-  CK(cudaGetLastError());
-  return LBM_OK;
+  return with_storage(h, [&](auto tag) -> int {
+    using ST = decltype(tag);
+    dim3 blk(128), grd((h->L.Nx + 127) / 128);
+    lbm_colsum_kernel<ST><<<grd, blk, 0, h->stream>>>(h->L, (const ST*)h->buf[b], h->refrho,
+                                                      h->cs[b]);
+    CK(cudaGetLastError());
+    return LBM_OK;
+  });
 }
 
 int reset_diag(lbm_mix* h) {
@@ -1119,28 +1256,33 @@ int reset_diag(lbm_mix* h) {
 }
 
 int launch_step(lbm_mix* h, bool diag) {
-  StepArgs<float> a;
   const int b = h->cur;
-  a.fin = h->buf[b];
-  a.fout = h->buf[1 - b];
-  a.refrho = h->refrho;
-  a.cs_in = h->cs[b];
-  a.cs_out = h->cs[1 - b];
-  a.alpha = h->alpha;
-  a.partials = h->partials;
-  a.counter = h->counter;
-  a.diag = h->diag;
-  a.diag_count = h->diag_count;
-  a.clprof = h->clprof;
-  a.colpart = h->colpart;
-  a.strip_cnt = h->strip_cnt;
-  a.rows_per_block = h->rows_per_block;
-  dim3 blk(TX, TY), grd(h->nblocks, h->R);
-  if (diag)
-    lbm_step_kernel<float, true><<<grd, blk, 0, h->stream>>>(h->L, a);
-  else
-    lbm_step_kernel<float, false><<<grd, blk, 0, h->stream>>>(h->L, a);
-  CK(cudaGetLastError());
+  int st = with_storage(h, [&](auto tag) -> int {
+    using ST = decltype(tag);
+    StepArgs<ST> a;
+    a.fin = (const ST*)h->buf[b];
+    a.fout = (ST*)h->buf[1 - b];
+    a.refrho = h->refrho;
+    a.cs_in = h->cs[b];
+    a.cs_out = h->cs[1 - b];
+    a.alpha = h->alpha;
+    a.partials = h->partials;
+    a.counter = h->counter;
+    a.diag = h->diag;
+    a.diag_count = h->diag_count;
+    a.clprof = h->clprof;
+    a.colpart = h->colpart;
+    a.strip_cnt = h->strip_cnt;
+    a.rows_per_block = h->rows_per_block;
+    dim3 blk(TX, TY), grd(h->nblocks, h->R);
+    if (diag)
+      lbm_step_kernel<ST, true><<<grd, blk, 0, h->stream>>>(h->L, a);
+    else
+      lbm_step_kernel<ST, false><<<grd, blk, 0, h->stream>>>(h->L, a);
+    CK(cudaGetLastError());
+    return LBM_OK;
+  });
+  if (st) return st;
   h->cur = 1 - b;
   h->steps++;
   return LBM_OK;
@@ -1152,9 +1294,14 @@ int launch_moments(lbm_mix* h, double* d_out) {
   const bool direct = (h->steps == 0);
   const int b = direct ? h->cur : 1 - h->cur;
   dim3 blk(TX, TY), grd(h->nblocks);
-  lbm_moments_kernel<float><<<grd, blk, 0, h->stream>>>(h->L, h->buf[b], h->refrho, h->cs[b],
-                                                        h->alpha, direct ? 1 : 0, d_out);
-  CK(cudaGetLastError());
+  int st = with_storage(h, [&](auto tag) -> int {
+    using ST = decltype(tag);
+    lbm_moments_kernel<ST><<<grd, blk, 0, h->stream>>>(h->L, (const ST*)h->buf[b], h->refrho,
+                                                       h->cs[b], h->alpha, direct ? 1 : 0, d_out);
+    CK(cudaGetLastError());
+    return LBM_OK;
+  });
+  if (st) return st;
   if (!h->L.x_periodic) {
     lbm_moments_ends_kernel<<<2, 256, 0, h->stream>>>(h->L, d_out);
     CK(cudaGetLastError());
@@ -1228,9 +1375,15 @@ int get_post_state_t(lbm_mix* h, T* f, long n) {
   // staging area sized for the FP64 variant, shared by both getters
   if (!h->scratch) CK(cudaMalloc((void**)&h->scratch, sizeof(double) * (size_t)need));
   dim3 blk(128), grd((h->L.Nx + 127) / 128, h->L.N, 2);
-  lbm_convert_kernel<float, T><<<grd, blk, 0, h->stream>>>(h->L, h->buf[h->cur], h->refrho, 0,
-                                                           nullptr, (T*)h->scratch);
-  CK(cudaGetLastError());
+  if ((st = with_storage(h, [&](auto tag) -> int {
+         using ST = decltype(tag);
+         lbm_convert_kernel<ST, T><<<grd, blk, 0, h->stream>>>(h->L, (ST*)h->buf[h->cur],
+                                                               h->refrho, 0, nullptr,
+                                                               (T*)h->scratch);
+         CK(cudaGetLastError());
+         return LBM_OK;
+       })))
+    return st;
   CK(cudaMemcpyAsync(f, h->scratch, bytes, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return LBM_OK;
@@ -1331,7 +1484,8 @@ int lbm_mix_create(const lbm_mix_params* p, void* stream, lbm_mix** out) {
     }
     h->own_stream = true;
   }
-  const size_t fbytes = sizeof(float) * 18 * (size_t)h->L.N * h->L.pitch;
+  h->elem = (p->storage == LBM_FP32) ? sizeof(float) : 2;
+  const size_t fbytes = h->elem * 18 * (size_t)h->L.N * h->L.pitch;
   const size_t cbytes = sizeof(double) * 4 * (size_t)Nx;
   cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, bytes) \
@@ -1418,7 +1572,7 @@ int lbm_mix_init(lbm_mix* h) {
   h->steps = 0;
   // the initial state is the rest equilibrium of the reference densities:
   // all stored deviations are zero
-  CK(cudaMemsetAsync(h->buf[0], 0, sizeof(float) * 18 * (size_t)h->L.N * h->L.pitch,
+  CK(cudaMemsetAsync(h->buf[0], 0, h->elem * 18 * (size_t)h->L.N * h->L.pitch,
                      h->stream));
   if ((st = launch_colsum(h, 0))) return st;
   return reset_diag(h);
@@ -1566,9 +1720,14 @@ int lbm_mix_set_post_state(lbm_mix* h, const float* f, long n) {
                      h->stream));
   {
     dim3 blk(128), grd((h->L.Nx + 127) / 128, h->L.N, 2);
-    lbm_convert_kernel<float, float><<<grd, blk, 0, h->stream>>>(
-        h->L, h->buf[0], h->refrho, 1, (const float*)h->scratch, (float*)nullptr);
-    CK(cudaGetLastError());
+    if ((st = with_storage(h, [&](auto tag) -> int {
+           using ST = decltype(tag);
+           lbm_convert_kernel<ST, float><<<grd, blk, 0, h->stream>>>(
+               h->L, (ST*)h->buf[0], h->refrho, 1, (const float*)h->scratch, (float*)nullptr);
+           CK(cudaGetLastError());
+           return LBM_OK;
+         })))
+      return st;
   }
   if ((st = launch_colsum(h, 0))) return st;
   if ((st = reset_diag(h))) return st;
@@ -1633,6 +1792,8 @@ int lbm_mix_step_noalloc(const lbm_mix_params* p, const float* d_in, float* d_ou
       !d_cl_profile)
     return set_err(LBM_EINVAL, "lbm_mix_step_noalloc: every buffer must be a device pointer");
   if (d_in == d_out) return set_err(LBM_EINVAL, "lbm_mix_step_noalloc: d_in and d_out alias");
+  if (p->storage != LBM_FP32)
+    return set_err(LBM_EINVAL, "lbm_mix_step_noalloc: FP32 storage only");
   const int nstrips = (Nx + TX - 1) / TX;
   if (nstrips > NOALLOC_MAX_STRIPS)
     return set_err(LBM_EINVAL,
