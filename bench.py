@@ -290,7 +290,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--cpu-steps", type=int, default=100)
+    ap.add_argument("--cpu-steps", type=int, default=1000)
     ap.add_argument("--diag-every", type=int, default=100,
                     help="steps between FP64 separation-diagnostic reductions (the column "
                          "sums of the end columns are reduced every step)")

@@ -258,6 +258,18 @@ __device__ __forceinline__ unsigned idx(const Lat& L, int sp, int i, int j, int 
   return (unsigned)(x >> 5) * L.SS + (unsigned)(j * RS + (sp * 9 + i) * TX + (x & 31));
 }
 
+// Bulk prefetch of one strip row (all 18 populations of 32 columns, one
+// contiguous RS-element run) into L2.  Issued by one lane per warp for the
+// row that warp sweeps next, so the DRAM reads of row j + TY are in flight
+// while row j is computed, with no registers or shared memory held for them.
+template <typename ST>
+__device__ __forceinline__ void prefetch_row_l2(const ST* row) {
+  static_assert((RS * sizeof(ST)) % 16 == 0, "bulk prefetch size must be a multiple of 16 B");
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(row),
+               "r"((int)(RS * sizeof(ST)))
+               : "memory");
+}
+
 template <typename ST>
 __device__ __forceinline__ float ld(const ST* __restrict__ f, const Lat& L, int sp, int i, int j,
                                     int x) {
@@ -855,6 +867,11 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
   const int x0 = blockIdx.x * TX, x = x0 + tx;
   const ColRef C = col_ref(L, a.refrho, x);
   const Ends E = load_ends(L, a.cs_in, a.refrho);
+  const int j_begin = blockIdx.y * a.rows_per_block;
+  const int j_end = min(L.N, j_begin + a.rows_per_block);
+  // the first row of each warp is read from L2 while the wall prologue runs
+  if (tx == 0 && j_begin + ty < j_end)
+    prefetch_row_l2(a.fin + (size_t)blockIdx.x * L.SS + (size_t)(j_begin + ty) * RS);
   wall_prologue<true>(L, a.fin, a.alpha, E, C, x, wsm);
   const bool in = interior(L, x);
   // strips holding column 1 or N_x - 2 take the general pull (ghost columns)
@@ -867,13 +884,14 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
   const float r_bot = wsm.r[0][tx], r_top = wsm.r[1][tx];
   const int half = (L.N + 1) / 2;  // rows j < half (1-based 2J <= N+1) use the bottom tau_q
   KahanF acc[4];
-  const int j_begin = blockIdx.y * a.rows_per_block;
-  const int j_end = min(L.N, j_begin + a.rows_per_block);
   const bool reduce = DIAG || edge_strip;
   if (in) {
     for (int j = j_begin + ty; j < j_end; j += TY) {
       float fs[2][9];
       const ST* p = a.fin + base + j * RS;
+      // row start is 16-byte aligned (RS * sizeof(ST) is a multiple of 16);
+      // the prefetched row lies inside this strip (j + TY < j_end <= N)
+      if (tx == 0 && j + TY < j_end) prefetch_row_l2(p + TY * RS);
       if (!edge_strip && j != 0 && j != L.N - 1)
         pull_fast(p, p + offl, p + offr, L, C, fs);
       else
