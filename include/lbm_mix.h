@@ -190,8 +190,9 @@ int lbm_mix_eval_special(const double* x, double* e1, double* psi, long n);
  *                 rest equilibrium (Eq. feq with u = 0; w_i alpha_si =
  *                 (9 - 5 s)/9, s/9, s/36 for rest, axis, diagonal
  *                 populations, s = m_min / m_sigma) of the reference density
- *                 rhobar; laid out in strips of 32 columns:
- *                 index = (x/32) * 576 N + j * 576 + (sigma * 9 + i) * 32 + x%32,
+ *                 rhobar; laid out in strips of 32 columns with the two
+ *                 species of a population adjacent:
+ *                 index = (x/32) * 576 N + j * 576 + i * 64 + 2 * (x%32) + sigma,
  *                 18 * N * 32 * ceil(N_x/32) floats each; must not alias;
  *   d_refrho      rhobar_s(x), [2][N_x] floats, any fixed positive profile
  *                 (the same one for every step of a run);

@@ -12,16 +12,17 @@
 // diagnostics (Eqs. C, CL, Clline).
 //
 // Data layout in HBM (per buffer): the channel is cut into strips of 32
-// columns; strip s holds, row after row, the 18 populations (species a then
-// b, i = 0..8) of its 32 columns as 128-byte segments:
-//   offset(sp, i, j, x) = (x / 32) * SS + j * RS + (sp * 9 + i) * 32 + x % 32
-// with RS = 576 floats per row block and SS = N * RS per strip.  A strip is
-// one contiguous region that its CTA streams through front to back, every
-// warp access is one aligned 128-byte segment, and all offsets inside a strip
-// are compile-time immediates.  Two buffers A/B alternate.  One CTA owns one
-// strip over ALL rows, sweeping rows in steps of TY, so that every per-column
-// quantity (the tau_q of the two walls, the column sums) is produced inside
-// one CTA without atomics and in a fixed order.
+// columns; strip s holds, row after row, the nine populations of its 32
+// columns, each as one segment of 32 species pairs (a, b):
+//   offset(sp, i, j, x) = (x / 32) * SS + j * RS + i * 64 + 2 * (x % 32) + sp
+// with RS = 576 elements per strip row and SS = N * RS per strip.  A node's
+// two species of population i are adjacent, so one 8-byte (FP32) or 4-byte
+// (BF16/FP16) access per lane fetches both and a warp access is one aligned
+// contiguous segment; all offsets inside a strip are compile-time
+// immediates.  Two buffers A/B alternate.  The CTAs of one strip (one per
+// row block) sweep their rows in steps of TY; the per-column quantities (the
+// tau_q of the two walls, the column sums) are produced by the CTAs of that
+// strip alone, without floating-point atomics and in a fixed order.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -61,7 +62,8 @@ int set_err(int code, const char* fmt, ...) {
 
 // ------------------------------------------------------- lattice constants
 constexpr int TX = 32;          // columns per CTA = strip width (one warp per row segment)
-constexpr int RS = 18 * TX;     // floats per row block of a strip
+constexpr int RS = 18 * TX;     // elements per row of a strip (9 populations x 32 pairs)
+constexpr int PS = 2 * TX;      // elements per population segment (32 columns x 2 species)
 constexpr int TY = 8;           // rows per sweep iteration
 constexpr int NPART = 8;        // doubles per CTA partial
 constexpr int NREC = 8;         // doubles per diagnostic record
@@ -227,10 +229,18 @@ __device__ __forceinline__ float2 psi2(float2 a) {
 // on deviations relative to the node's own column reference.
 template <typename ST>
 struct Stor;
+// ld/st move one species' value; ld2/st2 move the (a, b) pair of a node's
+// population at p (p points at species a, aligned to the pair).
 template <>
 struct Stor<float> {
   static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
   static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+  static __device__ __forceinline__ float2 ld2(const float* p) {
+    return __ldg(reinterpret_cast<const float2*>(p));
+  }
+  static __device__ __forceinline__ void st2(float* p, float2 v) {
+    *reinterpret_cast<float2*>(p) = v;
+  }
 };
 // Reduced-precision storage of the same deviations: loads widen to FP32, all
 // arithmetic is FP32, stores round to nearest.
@@ -242,11 +252,23 @@ struct Stor<__nv_bfloat16> {
   static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) {
     *p = __float2bfloat16_rn(v);
   }
+  static __device__ __forceinline__ float2 ld2(const __nv_bfloat16* p) {
+    return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
+  }
+  static __device__ __forceinline__ void st2(__nv_bfloat16* p, float2 v) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v);
+  }
 };
 template <>
 struct Stor<__half> {
   static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
   static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+  static __device__ __forceinline__ float2 ld2(const __half* p) {
+    return __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+  }
+  static __device__ __forceinline__ void st2(__half* p, float2 v) {
+    *reinterpret_cast<__half2*>(p) = __float22half2_rn(v);
+  }
 };
 
 struct Ends {
@@ -255,7 +277,7 @@ struct Ends {
 };
 
 __device__ __forceinline__ unsigned idx(const Lat& L, int sp, int i, int j, int x) {
-  return (unsigned)(x >> 5) * L.SS + (unsigned)(j * RS + (sp * 9 + i) * TX + (x & 31));
+  return (unsigned)(x >> 5) * L.SS + (unsigned)(j * RS + i * PS + 2 * (x & 31) + sp);
 }
 
 // Bulk prefetch of one strip row (all 18 populations of 32 columns, one
@@ -370,27 +392,23 @@ __device__ __forceinline__ void pull_node(const ST* __restrict__ f, const Lat& L
 }
 
 // The same pull for a node whose row is not a wall row and whose strip does
-// not contain an end column: nine plain loads per species at immediate
-// offsets from the row pointers of columns x (p), x - 1 (pl) and x + 1 (pr).
+// not contain an end column: nine pair loads (both species) at immediate
+// offsets from the row pointers of columns x (p), x - 1 (pl) and x + 1 (pr),
+// re-referenced to column x in FP32x2.
 template <typename ST>
 __device__ __forceinline__ void pull_fast(const ST* __restrict__ p, const ST* __restrict__ pl,
                                           const ST* __restrict__ pr, const Lat& L,
-                                          const ColRef& C, float fs[2][9]) {
-#pragma unroll
-  for (int sp = 0; sp < 2; ++sp) {
-    const int o = sp * 9 * TX;
-    const float c1 = L.cw1[sp], c5 = L.cw5[sp], dl = C.dl[sp], dr = C.dr[sp];
-    float* g = fs[sp];
-    g[0] = Stor<ST>::ld(p + o);
-    g[1] = fmaf(c1, dl, Stor<ST>::ld(pl + o + 1 * TX));
-    g[3] = fmaf(c1, dr, Stor<ST>::ld(pr + o + 3 * TX));
-    g[2] = Stor<ST>::ld(p + o + 2 * TX - RS);
-    g[5] = fmaf(c5, dl, Stor<ST>::ld(pl + o + 5 * TX - RS));
-    g[6] = fmaf(c5, dr, Stor<ST>::ld(pr + o + 6 * TX - RS));
-    g[4] = Stor<ST>::ld(p + o + 4 * TX + RS);
-    g[7] = fmaf(c5, dr, Stor<ST>::ld(pr + o + 7 * TX + RS));
-    g[8] = fmaf(c5, dl, Stor<ST>::ld(pl + o + 8 * TX + RS));
-  }
+                                          const ColRef& C, float2 g[9]) {
+  const float2 dl = make_float2(C.dl[0], C.dl[1]), dr = make_float2(C.dr[0], C.dr[1]);
+  g[0] = Stor<ST>::ld2(p);
+  g[1] = fma2(L.cw1_2, dl, Stor<ST>::ld2(pl + 1 * PS));
+  g[3] = fma2(L.cw1_2, dr, Stor<ST>::ld2(pr + 3 * PS));
+  g[2] = Stor<ST>::ld2(p + 2 * PS - RS);
+  g[5] = fma2(L.cw5_2, dl, Stor<ST>::ld2(pl + 5 * PS - RS));
+  g[6] = fma2(L.cw5_2, dr, Stor<ST>::ld2(pr + 6 * PS - RS));
+  g[4] = Stor<ST>::ld2(p + 4 * PS + RS);
+  g[7] = fma2(L.cw5_2, dr, Stor<ST>::ld2(pr + 7 * PS + RS));
+  g[8] = fma2(L.cw5_2, dl, Stor<ST>::ld2(pl + 8 * PS + RS));
 }
 
 // ---------------------------------------------------------------- moments
@@ -879,7 +897,7 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
   int xm = x - 1, xp = x + 1;
   if (xm < 0) xm += L.Nx;
   if (xp >= L.Nx) xp -= L.Nx;
-  const unsigned base = blockIdx.x * L.SS + tx;  // row 0, species a, i = 0 of column x
+  const unsigned base = blockIdx.x * L.SS + 2 * tx;  // row 0, i = 0, species a of column x
   const int offl = (int)(idx(L, 0, 0, 0, xm) - base), offr = (int)(idx(L, 0, 0, 0, xp) - base);
   const float r_bot = wsm.r[0][tx], r_top = wsm.r[1][tx];
   const int half = (L.N + 1) / 2;  // rows j < half (1-based 2J <= N+1) use the bottom tau_q
@@ -887,18 +905,19 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
   const bool reduce = DIAG || edge_strip;
   if (in) {
     for (int j = j_begin + ty; j < j_end; j += TY) {
-      float fs[2][9];
+      float2 g[9];
       const ST* p = a.fin + base + j * RS;
       // row start is 16-byte aligned (RS * sizeof(ST) is a multiple of 16);
       // the prefetched row lies inside this strip (j + TY < j_end <= N)
       if (tx == 0 && j + TY < j_end) prefetch_row_l2(p + TY * RS);
-      if (!edge_strip && j != 0 && j != L.N - 1)
-        pull_fast(p, p + offl, p + offr, L, C, fs);
-      else
+      if (!edge_strip && j != 0 && j != L.N - 1) {
+        pull_fast(p, p + offl, p + offr, L, C, g);
+      } else {
+        float fs[2][9];
         pull_node(a.fin, L, E, C, x, j, r_bot, r_top, fs);
-      float2 g[9];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) g[i] = make_float2(fs[0][i], fs[1][i]);
+        for (int i = 0; i < 9; ++i) g[i] = make_float2(fs[0][i], fs[1][i]);
+      }
       Macro2 m;
       macro2(L, C, g, m);
       float om_s, om_d;
@@ -914,10 +933,7 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
       }
       ST* o = a.fout + base + j * RS;
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        Stor<ST>::st(o + i * TX, g[i].x);
-        Stor<ST>::st(o + (9 + i) * TX, g[i].y);
-      }
+      for (int i = 0; i < 9; ++i) Stor<ST>::st2(o + i * PS, g[i]);
     }
   }
   if (!reduce) return;  // CTA-uniform

@@ -33,16 +33,16 @@ def _weights(p):
 
 
 def _to_strips(d, N, Nx):
-    """[2][9][N][Nx] -> strip layout (x/32) * 576 N + j * 576 + (sp*9 + i)*32 + x%32."""
+    """[2][9][N][Nx] -> strip layout (x/32) * 576 N + j * 576 + i * 64 + 2 * (x%32) + sp."""
     S = (Nx + 31) // 32
     pad = np.zeros((2, 9, N, S * 32), dtype=d.dtype)
     pad[..., :Nx] = d
-    return np.ascontiguousarray(pad.reshape(2, 9, N, S, 32).transpose(3, 2, 0, 1, 4)).ravel()
+    return np.ascontiguousarray(pad.reshape(2, 9, N, S, 32).transpose(3, 2, 1, 4, 0)).ravel()
 
 
 def _from_strips(flat, N, Nx):
     S = (Nx + 31) // 32
-    a = flat.reshape(S, N, 2, 9, 32).transpose(2, 3, 1, 0, 4).reshape(2, 9, N, S * 32)
+    a = flat.reshape(S, N, 9, 32, 2).transpose(4, 2, 1, 0, 3).reshape(2, 9, N, S * 32)
     return a[..., :Nx]
 
 
