@@ -233,6 +233,27 @@ def run_ours(args):
     h2d = f_np.nbytes
     d2h = sum(a.nbytes for a in ptrs) + 8 * (sim.N_x + 8)
 
+    # ---------------- reduced-precision storage on the same workload (device timing)
+    variants = {}
+    if not args.no_variants:
+        for name, storage in (("bf16", binding.LBM_BF16), ("fp16", binding.LBM_FP16)):
+            v = binding.LbmMix(stream=stream, storage=storage, **p)
+            v.init()
+            binding.lbm_mix_step(v.h, args.warmup)
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            binding.lbm_mix_step(v.h, args.steps)
+            e1.record(stream)
+            e1.synchronize()
+            t_v = e0.elapsed_time(e1) / 1e3 / args.steps
+            variants[name] = {"ms_per_step": t_v * 1e3, "value": nodes / t_v / 1e6,
+                              "unit": "MLUPS", "bytes_per_node_step": BYTES_PER_NODE // 2,
+                              "achieved_gbs": BYTES_PER_NODE // 2 * nodes / t_v / 1e9,
+                              "reref_every": 256}
+            del v
+
     # ---------------- whole-job aggregation (max time over ranks)
     if world > 1:
         import torch.distributed as dist
@@ -273,6 +294,7 @@ def run_ours(args):
         "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h / args.steps},
         "gpu_launches": args.steps,
+        "storage_variants": variants or None,
         "clocks": clk.summary(),
         "result": {"CL": sep["CL"], "Cl_tilde": sep["Cl_tilde"], "mdot_a": sep["mdot_a"],
                    "mdot_b": sep["mdot_b"], "CL_e2e_run": sep_e2e["CL"]},
@@ -295,6 +317,8 @@ def main():
                     help="steps between FP64 separation-diagnostic reductions (the column "
                          "sums of the end columns are reduced every step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the BF16/FP16 storage timings")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

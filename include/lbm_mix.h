@@ -68,12 +68,15 @@ typedef struct {
   int storage;          /* LBM_FP32, LBM_BF16 or LBM_FP16 */
   int x_periodic;       /* 1: periodic in x instead of pressure ends */
   int diag_every;       /* >= 1: steps between separation-diagnostic reductions */
+  int reref_every;      /* steps between re-referencings of the stored deviations
+                           (lbm_mix_rereference); 0 = never; -1 = 256 for BF16/FP16
+                           storage and never for FP32 */
 } lbm_mix_params;
 
 /* Fills the defaults: He-Ar (4.003, 39.948), C_l = 0.5, C_l_out = -1,
  * theta = 2, Kn_out = 0.1, N = 16, N_x = 0, L_over_H = 20, alpha = 1,
  * c_m0 = 1.016, tau_rho = 1, tau_e = 1.1, tau_eps = 1.2, mu ratios 1,
- * LBM_FP32, x_periodic = 0, diag_every = 1.  NULL-safe. */
+ * LBM_FP32, x_periodic = 0, diag_every = 1, reref_every = -1.  NULL-safe. */
 void lbm_mix_default_params(lbm_mix_params* p);
 
 /* Validates p, derives the lattice constants (Eqs. P, EQFrb, rho2 with the
@@ -98,8 +101,23 @@ int lbm_mix_init(lbm_mix* h);
  * diag_every-th step (counted from init) and of the last step of the call
  * also reduces the separation diagnostics of the new state in FP64 (one
  * history record each), so lbm_mix_separation after lbm_mix_step always
- * describes the current state. */
+ * describes the current state.  After every reref_every-th step (counted
+ * from init) the stored deviations are re-referenced (lbm_mix_rereference). */
 int lbm_mix_step(lbm_mix* h, long nsteps);
+
+/* Re-references the stored state: the populations are kept as deviations
+ * d_i = f_i - w_i alpha_si rhobar_s(x) from the rest equilibrium (Eq. feq,
+ * u = 0) of a per-column reference density, initially the profile of
+ * lbm_mix_init.  This sets rhobar_s(x) to the current column mean
+ * (1/N) sum_j rho_s(x, j) of every updated column and rewrites the
+ * deviations to match, so that they stay small as the flow departs from its
+ * initial state: f itself changes only by one rounding of the storage type.
+ * With BF16/FP16 storage the deviations' precision is relative to their
+ * size, which is why lbm_mix_step does this periodically there.  One pass
+ * over both population buffers plus a column reduction, asynchronous on the
+ * handle's stream.  No counterpart in the paper (a storage device, not physics).
+ * Errors: LBM_EINVAL for a bad handle, LBM_ECUDA. */
+int lbm_mix_rereference(lbm_mix* h);
 
 /* Steps in blocks of `check_every` (>= 1) until the steady-state residual
  * R = |c(t) - c(t-K)|_2 / (K |c(t)|_2) of the column-integrated species

@@ -42,6 +42,7 @@ class lbm_mix_params(ctypes.Structure):
         ("mu_ratio_a", ctypes.c_double), ("mu_ratio_b", ctypes.c_double),
         ("storage", ctypes.c_int), ("x_periodic", ctypes.c_int),
         ("diag_every", ctypes.c_int),
+        ("reref_every", ctypes.c_int),
     ]
 
 
@@ -65,6 +66,7 @@ _SIGS = {
     "lbm_mix_destroy": (None, [_H]),
     "lbm_mix_init": (_I, [_H]),
     "lbm_mix_step": (_I, [_H, _L]),
+    "lbm_mix_rereference": (_I, [_H]),
     "lbm_mix_run_to_steady": (_I, [_H, _D, _L, _L, ctypes.POINTER(_L), _PD]),
     "lbm_mix_moments": (_I, [_H, _PD, _PD, _PD, _PD, _PD, _PD]),
     "lbm_mix_moments_device": (_I, [_H, ctypes.c_void_p]),
@@ -151,6 +153,10 @@ def lbm_mix_init(h) -> None:
 
 def lbm_mix_step(h, nsteps: int) -> None:
     _check(load().lbm_mix_step(h, int(nsteps)), "lbm_mix_step")
+
+
+def lbm_mix_rereference(h) -> None:
+    _check(load().lbm_mix_rereference(h), "lbm_mix_rereference")
 
 
 def lbm_mix_run_to_steady(h, tol: float, max_steps: int, check_every: int):
@@ -306,6 +312,9 @@ class LbmMix:
 
     def step(self, n: int = 1):
         lbm_mix_step(self.h, n)
+
+    def rereference(self):
+        lbm_mix_rereference(self.h)
 
     def sync(self):
         lbm_mix_sync(self.h)

@@ -156,7 +156,7 @@ __device__ __forceinline__ float psi_dev(float a) {
     // __logf: absolute error ~2^-21 on ln a near a = 1, i.e. < 2e-7 in a^2 ln a
     return fmaf(a * a, __logf(a), q * a);
   }
-  if (a >= 15.0f) return 1.0f;
+  if (a >= 16.0f) return 1.0f;  // 1 - psi(a) < 2 e^{-a}/a < 2^{-25}
   float num = (((a + 8.5733287401f) * a + 18.0590169730f) * a + 8.6347608925f) * a +
               0.2677737343f;
   float den = (((a + 9.5733223454f) * a + 25.6329561486f) * a + 21.0996530827f) * a +
@@ -185,38 +185,58 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
   return __ffma2_rn(b, f2(-1.0f), a);  // exact: a - b with one rounding
 }
 
-// psi at two arguments at once without branches: both formulas of psi_dev
-// are evaluated (on min(a, 1) and max(a, 1)) and the right one selected.
+// psi at two arguments at once.  The lanes of a warp sweep one row (the same
+// y) of 32 neighbouring columns, whose mean free paths differ little, so with
+// SKIP the two formulas of psi_dev are taken as warp-uniform branches: the
+// entire-part series when some lane has an argument <= 1, the rational form
+// when some lane has one in (1, 16).  Without SKIP both are evaluated and
+// selected (straight-line code that the compiler can interleave with the
+// loads of a memory-bound sweep).  At a >= 16, 1 - psi(a) < 2 e^{-a}/a <
+// 2^{-25} rounds away and psi = 1.
+template <bool SKIP>
 __device__ __forceinline__ float2 psi2(float2 a) {
-  const float2 as = make_float2(fminf(a.x, 1.0f), fminf(a.y, 1.0f));
-  float2 q = f2(-1.0f / 179625600.0f);
-  q = fma2(q, as, f2(1.0f / 14515200.0f));
-  q = fma2(q, as, f2(-1.0f / 1270080.0f));
-  q = fma2(q, as, f2(1.0f / 120960.0f));
-  q = fma2(q, as, f2(-1.0f / 12600.0f));
-  q = fma2(q, as, f2(1.0f / 1440.0f));
-  q = fma2(q, as, f2(-1.0f / 180.0f));
-  q = fma2(q, as, f2(1.0f / 24.0f));
-  q = fma2(q, as, f2(-1.0f / 3.0f));
-  q = fma2(q, as, f2(0.5772156649f - 1.5f));
-  q = fma2(q, as, f2(2.0f));
-  const float2 lg = make_float2(__logf(as.x), __logf(as.y));
-  const float2 ps = fma2(mul2(as, as), lg, mul2(q, as));
-  const float2 al = make_float2(fmaxf(a.x, 1.0f), fmaxf(a.y, 1.0f));
-  float2 num = add2(al, f2(8.5733287401f));
-  num = fma2(num, al, f2(18.0590169730f));
-  num = fma2(num, al, f2(8.6347608925f));
-  num = fma2(num, al, f2(0.2677737343f));
-  float2 den = add2(al, f2(9.5733223454f));
-  den = fma2(den, al, f2(25.6329561486f));
-  den = fma2(den, al, f2(21.0996530827f));
-  den = fma2(den, al, f2(3.9584969228f));
-  const float2 R = make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
-  const float2 e = make_float2(__expf(-al.x), __expf(-al.y));
-  // 1 + e^{-a} [(a - 1) - a R]
-  const float2 pl = fma2(e, fma2(make_float2(-al.x, -al.y), R, add2(al, f2(-1.0f))), f2(1.0f));
-  return make_float2(a.x <= 1.0f ? (a.x > 0.0f ? ps.x : 0.0f) : pl.x,
-                     a.y <= 1.0f ? (a.y > 0.0f ? ps.y : 0.0f) : pl.y);
+  const bool small = (a.x <= 1.0f) || (a.y <= 1.0f);
+  const bool mid = (a.x > 1.0f && a.x < 16.0f) || (a.y > 1.0f && a.y < 16.0f);
+  bool do_small = true, do_mid = true;
+  if (SKIP) {
+    const unsigned lanes = __activemask();
+    do_small = __any_sync(lanes, small);
+    do_mid = __any_sync(lanes, mid);
+  }
+  float2 ps = f2(0.0f), pl = f2(1.0f);
+  if (do_small) {
+    const float2 as = make_float2(fminf(a.x, 1.0f), fminf(a.y, 1.0f));
+    float2 q = f2(-1.0f / 179625600.0f);
+    q = fma2(q, as, f2(1.0f / 14515200.0f));
+    q = fma2(q, as, f2(-1.0f / 1270080.0f));
+    q = fma2(q, as, f2(1.0f / 120960.0f));
+    q = fma2(q, as, f2(-1.0f / 12600.0f));
+    q = fma2(q, as, f2(1.0f / 1440.0f));
+    q = fma2(q, as, f2(-1.0f / 180.0f));
+    q = fma2(q, as, f2(1.0f / 24.0f));
+    q = fma2(q, as, f2(-1.0f / 3.0f));
+    q = fma2(q, as, f2(0.5772156649f - 1.5f));
+    q = fma2(q, as, f2(2.0f));
+    const float2 lg = make_float2(__logf(as.x), __logf(as.y));
+    ps = fma2(mul2(as, as), lg, mul2(q, as));
+  }
+  if (do_mid) {
+    const float2 al = make_float2(fmaxf(a.x, 1.0f), fmaxf(a.y, 1.0f));
+    float2 num = add2(al, f2(8.5733287401f));
+    num = fma2(num, al, f2(18.0590169730f));
+    num = fma2(num, al, f2(8.6347608925f));
+    num = fma2(num, al, f2(0.2677737343f));
+    float2 den = add2(al, f2(9.5733223454f));
+    den = fma2(den, al, f2(25.6329561486f));
+    den = fma2(den, al, f2(21.0996530827f));
+    den = fma2(den, al, f2(3.9584969228f));
+    const float2 R = make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+    const float2 e = make_float2(__expf(-al.x), __expf(-al.y));
+    // 1 + e^{-a} [(a - 1) - a R]
+    pl = fma2(e, fma2(make_float2(-al.x, -al.y), R, add2(al, f2(-1.0f))), f2(1.0f));
+  }
+  return make_float2(a.x <= 1.0f ? (a.x > 0.0f ? ps.x : 0.0f) : (a.x < 16.0f ? pl.x : 1.0f),
+                     a.y <= 1.0f ? (a.y > 0.0f ? ps.y : 0.0f) : (a.y < 16.0f ? pl.y : 1.0f));
 }
 
 // ------------------------------------------------------------- storage
@@ -470,6 +490,7 @@ __device__ __forceinline__ void macro2(const Lat& L, const ColRef& C, const floa
 // with the wall-confinement factor Psi(y) = (psi(y/lambda) + psi((H-y)/lambda))/2
 // of the effective mean free path; the six psi values come from three packed
 // evaluations.
+template <bool SKIP>
 __device__ __forceinline__ void rates2(const Lat& L, const Macro2& m, float y, float& om_s,
                                        float& om_d) {
   const float rs_mx = rsqrtf(m.mx);
@@ -477,9 +498,9 @@ __device__ __forceinline__ void rates2(const Lat& L, const Macro2& m, float y, f
   const float inv_lam = L.inv_c_lam * m.n * (m.mx * rs_mx);  // 1 / lambda
   const float2 yy = make_float2(y, L.H - y);
   const float2 inv_ls = mul2(mul2(m.rho, L.s2), L.inv_c_xl2);  // 1 / lambda_s
-  const float2 pm = psi2(mul2(yy, f2(inv_lam)));
-  const float2 pa = psi2(mul2(yy, f2(inv_ls.x)));
-  const float2 pb = psi2(mul2(yy, f2(inv_ls.y)));
+  const float2 pm = psi2<SKIP>(mul2(yy, f2(inv_lam)));
+  const float2 pa = psi2<SKIP>(mul2(yy, f2(inv_ls.x)));
+  const float2 pb = psi2<SKIP>(mul2(yy, f2(inv_ls.y)));
   const float ts = lam * (0.5f * (pm.x + pm.y)) * L.c_ts * rs_mx;  // tau_s - 1/2
   om_s = __fdividef(1.0f, 0.5f + ts);
   // x_s lambda_se = c_xl / n * Psi(y; lambda_s)
@@ -921,7 +942,9 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
       Macro2 m;
       macro2(L, C, g, m);
       float om_s, om_d;
-      rates2(L, m, (float)j + 0.5f, om_s, om_d);
+      // 16-bit storage halves the bytes and leaves the sweep bound by
+      // instruction issue: there skipping psi work pays, for FP32 it does not
+      rates2<(sizeof(ST) < 4)>(L, m, (float)j + 0.5f, om_s, om_d);
       const float om_q = wsm.om_q[j < half ? 0 : 1][tx];
       const float2 mxs =
           collide2(g, L, m.rho, m.ux, m.uy, L.om_e, L.om_eps, om_d, om_q, om_s);
@@ -982,7 +1005,7 @@ __global__ void __launch_bounds__(TX* TY)
     Macro2 m;
     macro2(L, C, g, m);
     float om_s, om_d;
-    rates2(L, m, (float)j + 0.5f, om_s, om_d);
+    rates2<false>(L, m, (float)j + 0.5f, om_s, om_d);
     // Eq. rhou: (2 tau_d - 1)/(2 tau_d) = 1 - om_d/2, 1/(2 tau_d) = om_d/2
     const float w1 = 1.0f - 0.5f * om_d, w2 = 0.5f * om_d;
     const size_t o = (size_t)j * L.Nx + x;
@@ -1054,6 +1077,38 @@ __global__ void lbm_colsum_kernel(Lat L, const ST* __restrict__ f,
     }
     cs[(size_t)sp * L.Nx + x] = (double)L.N * (double)refrho[sp * L.Nx + x] + r;
     cs[(size_t)(2 + sp) * L.Nx + x] = m;
+  }
+}
+
+// Re-referencing: new reference rhobar'_s(x) = cs[s][x] / N (the column
+// mean of the current state) for the updated columns, unchanged elsewhere;
+// d_i <- d_i + w_i alpha_si (rhobar_s - rhobar'_s) in place, in both
+// buffers (the moments of the current step are formed by streaming the
+// previous one).  One thread per (x, j), both species of a population as
+// one pair.
+template <typename ST>
+__global__ void lbm_reref_kernel(Lat L, ST* __restrict__ f, ST* __restrict__ f_prev,
+                                 const float* __restrict__ ref_old,
+                                 const double* __restrict__ cs, float* __restrict__ ref_new) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (x >= L.Nx) return;
+  float2 ro = make_float2(ref_old[x], ref_old[L.Nx + x]), rn = ro;
+  if (interior(L, x))
+    rn = make_float2((float)(cs[x] / L.N), (float)(cs[L.Nx + x] / L.N));
+  if (j == 0) {
+    ref_new[x] = rn.x;
+    ref_new[L.Nx + x] = rn.y;
+  }
+  const float2 dr = sub2(ro, rn);
+  ST* p = f + idx(L, 0, 0, j, x);
+  ST* q = f_prev + idx(L, 0, 0, j, x);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const float2 cw = i == 0 ? make_float2(L.cw0[0], L.cw0[1])
+                             : (i < 5 ? L.cw1_2 : L.cw5_2);
+    Stor<ST>::st2(p + i * PS, fma2(cw, dr, Stor<ST>::ld2(p + i * PS)));
+    Stor<ST>::st2(q + i * PS, fma2(cw, dr, Stor<ST>::ld2(q + i * PS)));
   }
 }
 
@@ -1132,6 +1187,8 @@ struct lbm_mix {
   void* buf[2];       // post-collision deviations, A/B (element type per storage)
   size_t elem;        // bytes per stored population
   float* refrho;      // [2][Nx] reference densities rhobar_s(x)
+  float* refrho_alt;  // the next reference table of lbm_mix_rereference
+  double* cs_tmp;     // [4][Nx] column sums of lbm_mix_rereference
   float* scratch;     // full-population staging for get_post_state (lazy)
   double* cs[2];
   double* cs_snap;
@@ -1182,6 +1239,7 @@ int validate(const lbm_mix_params* p, int* Nx_out) {
     return set_err(LBM_EINVAL, "storage must be LBM_FP32, LBM_BF16 or LBM_FP16");
   if (p->x_periodic != 0 && p->x_periodic != 1) return set_err(LBM_EINVAL, "x_periodic is 0 or 1");
   if (p->diag_every < 1) return set_err(LBM_EINVAL, "diag_every must be >= 1");
+  if (p->reref_every < -1) return set_err(LBM_EINVAL, "reref_every must be >= -1");
   long pitch = (Nx + 31) / 32 * 32;
   double elems = 18.0 * (double)p->N * (double)pitch;
   if (elems >= 2147483648.0)
@@ -1280,6 +1338,29 @@ int launch_colsum(lbm_mix* h, int b) {
     CK(cudaGetLastError());
     return LBM_OK;
   });
+}
+
+// Column sums of the current state into cs_tmp, then the in-place rewrite
+// of the deviations against the new column means; the reference tables swap.
+int rereference(lbm_mix* h) {
+  const int b = h->cur;
+  int st = with_storage(h, [&](auto tag) -> int {
+    using ST = decltype(tag);
+    dim3 blk(128), grd((h->L.Nx + 127) / 128);
+    lbm_colsum_kernel<ST><<<grd, blk, 0, h->stream>>>(h->L, (const ST*)h->buf[b], h->refrho,
+                                                      h->cs_tmp);
+    CK(cudaGetLastError());
+    dim3 grd2((h->L.Nx + 127) / 128, h->L.N);
+    lbm_reref_kernel<ST><<<grd2, blk, 0, h->stream>>>(h->L, (ST*)h->buf[b], (ST*)h->buf[1 - b],
+                                                      h->refrho, h->cs_tmp, h->refrho_alt);
+    CK(cudaGetLastError());
+    return LBM_OK;
+  });
+  if (st) return st;
+  float* t = h->refrho;
+  h->refrho = h->refrho_alt;
+  h->refrho_alt = t;
+  return LBM_OK;
 }
 
 int reset_diag(lbm_mix* h) {
@@ -1447,6 +1528,7 @@ void lbm_mix_default_params(lbm_mix_params* p) {
   p->storage = LBM_FP32;
   p->x_periodic = 0;
   p->diag_every = 1;
+  p->reref_every = -1;
 }
 
 const char* lbm_mix_strerror(int s) {
@@ -1473,6 +1555,8 @@ void lbm_mix_destroy(lbm_mix* h) {
   cudaFree(h->buf[0]);
   cudaFree(h->buf[1]);
   cudaFree(h->refrho);
+  cudaFree(h->refrho_alt);
+  cudaFree(h->cs_tmp);
   cudaFree(h->scratch);
   cudaFree(h->cs[0]);
   cudaFree(h->cs[1]);
@@ -1527,6 +1611,8 @@ int lbm_mix_create(const lbm_mix_params* p, void* stream, lbm_mix** out) {
   ALLOC(h->buf[0], fbytes);
   ALLOC(h->buf[1], fbytes);
   ALLOC(h->refrho, sizeof(float) * 2 * (size_t)Nx);
+  ALLOC(h->refrho_alt, sizeof(float) * 2 * (size_t)Nx);
+  ALLOC(h->cs_tmp, cbytes);
   ALLOC(h->cs[0], cbytes);
   ALLOC(h->cs[1], cbytes);
   ALLOC(h->cs_snap, cbytes);
@@ -1616,12 +1702,21 @@ int lbm_mix_step(lbm_mix* h, long nsteps) {
   int st = check_handle(h);
   if (st) return st;
   if (nsteps < 0) return set_err(LBM_EINVAL, "nsteps < 0");
+  const long reref = h->p.reref_every >= 0 ? h->p.reref_every
+                                           : (h->p.storage == LBM_FP32 ? 0 : 256);
   // diagnostics on every diag_every-th step and on the last step of the call
   for (long t = 0; t < nsteps; ++t) {
     const bool diag = (t == nsteps - 1) || ((h->steps + 1) % h->p.diag_every == 0);
     if ((st = launch_step(h, diag))) return st;
+    if (reref > 0 && h->steps % reref == 0 && (st = rereference(h))) return st;
   }
   return LBM_OK;
+}
+
+int lbm_mix_rereference(lbm_mix* h) {
+  int st = check_handle(h);
+  if (st) return st;
+  return rereference(h);
 }
 
 int lbm_mix_run_to_steady(lbm_mix* h, double tol, long max_steps, long check_every,

@@ -49,12 +49,14 @@ def test_default_params(lib):
     assert p.m_a == 4.003 and p.m_b == 39.948 and p.C_l == 0.5
     assert p.tau_e == 1.1 and p.tau_eps == 1.2 and p.c_m0 == 1.016
     assert p.N == 16 and p.L_over_H == 20.0 and p.storage == binding.LBM_FP32
+    # the last fields: a ctypes mirror out of step with the C struct fails here
+    assert p.diag_every == 1 and p.reref_every == -1
 
 
 @pytest.mark.parametrize("field,value", [
     ("C_l", 0.0), ("C_l", 1.0), ("theta", 0.5), ("Kn_out", 0.0), ("N", 1), ("m_a", -1.0),
     ("accommodation", 0.0), ("accommodation", 1.5), ("tau_e", 0.5), ("storage", 7),
-    ("L_over_H", 0.1), ("x_periodic", 2),
+    ("L_over_H", 0.1), ("x_periodic", 2), ("diag_every", 0), ("reref_every", -2),
 ])
 def test_invalid_parameters_rejected_without_gpu(lib, field, value):
     p = binding.lbm_mix_default_params()
