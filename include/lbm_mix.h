@@ -234,6 +234,70 @@ int lbm_mix_step_noalloc(const lbm_mix_params* p, const float* d_in, float* d_ou
                          double* d_colsum_out, double* d_record, double* d_cl_profile,
                          void* stream);
 
+/* Node-to-CTA schedule of h: rows of one strip handled by one CTA of the
+ * step kernel, a multiple of 8 (capped at N rounded up to 8); 0 restores the
+ * library default (row blocks of at most 128 rows).  Changes only the order
+ * of the FP64 column reductions.  May allocate; not during stream capture.
+ * Errors: LBM_EINVAL (bad handle, rows not a multiple of 8), LBM_ENOMEM,
+ * LBM_ECUDA. */
+int lbm_mix_set_rows_per_block(lbm_mix* h, int rows);
+
+/* ---------------------------------------------------------------------
+ * Parametric sweeps (the study of Table 1 and Sec. 4: many independent
+ * channels).  No counterpart in the paper's method: a batching device.
+ *
+ * A sweep owns n handles, each on its own CUDA stream.  K steps of an
+ * instance are captured once as a CUDA graph and replayed, so each
+ * convergence check costs the host one graph launch per instance and the
+ * instances' step kernels run concurrently on the GPU.  FP32 storage only;
+ * every instance's diag_every is set to the check interval.
+ * ------------------------------------------------------------------- */
+typedef struct lbm_sweep lbm_sweep;
+
+/* Node-to-CTA schedules the autotuner tries: 0 library default (<= 128 rows
+ * per CTA), 1: 64, 2: 32, 3: 16 rows, 4: enough rows per CTA to give each
+ * instance about two CTAs per SM. */
+#define LBM_SWEEP_NPOLICY 5
+
+/* Creates n instances from params[0..n-1] (validated like lbm_mix_create)
+ * on the current device.  Errors: LBM_EINVAL (bad n, bad parameters of
+ * some instance, BF16/FP16 storage), LBM_ENOMEM, LBM_ECUDA. */
+int lbm_sweep_create(const lbm_mix_params* params, int n, lbm_sweep** out);
+
+/* Releases the sweep and all its instances.  NULL-safe. */
+void lbm_sweep_destroy(lbm_sweep* s);
+
+/* lbm_mix_init on every instance. */
+int lbm_sweep_init(lbm_sweep* s);
+
+/* nsteps plain steps on every instance (each on its stream), then waits
+ * for all of them. */
+int lbm_sweep_step(lbm_sweep* s, long nsteps);
+
+/* Every instance steps in blocks of check_every (even, >= 2) with the
+ * convergence test of lbm_mix_run_to_steady (same residual, same block
+ * boundaries, so the same step counts as a lone run) until its residual
+ * drops to tol (status LBM_OK), it has taken max_steps (LBM_ENOTCONVERGED)
+ * or turns non-finite (LBM_ENONFINITE); converged instances stop stepping.
+ * autotune != 0: the first LBM_SWEEP_NPOLICY blocks run under each
+ * node-to-CTA schedule in turn (real steps, timed on the host around the
+ * whole block), the rest under the fastest.  steps_out, residual_out,
+ * status_out: n entries each, nullable.  Returns LBM_OK when the sweep ran
+ * (per-instance outcomes are in status_out), LBM_EINVAL, LBM_ECUDA. */
+int lbm_sweep_run_to_steady(lbm_sweep* s, double tol, long max_steps, long check_every,
+                            int autotune, long* steps_out, double* residual_out,
+                            int* status_out);
+
+/* Borrowed handle of instance k (0 <= k < n): separation, moments and
+ * post-state getters work on it; it stays owned by the sweep. */
+int lbm_sweep_instance(lbm_sweep* s, int k, lbm_mix** out);
+
+/* Schedule in use (policy: -1 before any run, else 0..LBM_SWEEP_NPOLICY-1),
+ * rows per CTA of every instance (n entries) and the block times the
+ * autotuner measured per policy in ms (LBM_SWEEP_NPOLICY entries, 0 where
+ * not measured).  All outputs nullable. */
+int lbm_sweep_schedule(lbm_sweep* s, int* policy, int* rows_per_block, double* round_ms);
+
 /* Static description of an error code; never NULL. */
 const char* lbm_mix_strerror(int status);
 

@@ -80,6 +80,16 @@ _SIGS = {
     "lbm_mix_sync": (_I, [_H]),
     "lbm_mix_eval_special": (_I, [_PD, _PD, _PD, _L]),
     "lbm_mix_step_noalloc": (_I, [ctypes.POINTER(lbm_mix_params)] + [ctypes.c_void_p] * 9),
+    "lbm_mix_set_rows_per_block": (_I, [_H, _I]),
+    "lbm_sweep_create": (_I, [ctypes.POINTER(lbm_mix_params), _I,
+                              ctypes.POINTER(ctypes.c_void_p)]),
+    "lbm_sweep_destroy": (None, [_H]),
+    "lbm_sweep_init": (_I, [_H]),
+    "lbm_sweep_step": (_I, [_H, _L]),
+    "lbm_sweep_run_to_steady": (_I, [_H, _D, _L, _L, _I, ctypes.POINTER(_L), _PD,
+                                     ctypes.POINTER(_I)]),
+    "lbm_sweep_instance": (_I, [_H, _I, ctypes.POINTER(ctypes.c_void_p)]),
+    "lbm_sweep_schedule": (_I, [_H, ctypes.POINTER(_I), ctypes.POINTER(_I), _PD]),
     "lbm_mix_strerror": (ctypes.c_char_p, [_I]),
     "lbm_mix_last_error": (ctypes.c_char_p, []),
 }
@@ -282,18 +292,85 @@ def make_params(**kw) -> lbm_mix_params:
     return p
 
 
+def lbm_mix_set_rows_per_block(h, rows: int) -> None:
+    _check(load().lbm_mix_set_rows_per_block(h, int(rows)), "lbm_mix_set_rows_per_block")
+
+
+LBM_SWEEP_NPOLICY = 5
+
+
+def lbm_sweep_create(params_list) -> ctypes.c_void_p:
+    arr = (lbm_mix_params * len(params_list))(*params_list)
+    h = ctypes.c_void_p()
+    _check(load().lbm_sweep_create(arr, len(params_list), ctypes.byref(h)), "lbm_sweep_create")
+    return h
+
+
+def lbm_sweep_destroy(s) -> None:
+    load().lbm_sweep_destroy(s)
+
+
+def lbm_sweep_init(s) -> None:
+    _check(load().lbm_sweep_init(s), "lbm_sweep_init")
+
+
+def lbm_sweep_step(s, nsteps: int) -> None:
+    _check(load().lbm_sweep_step(s, int(nsteps)), "lbm_sweep_step")
+
+
+def lbm_sweep_run_to_steady(s, n: int, tol: float, max_steps: int, check_every: int,
+                            autotune: bool):
+    steps = (_L * n)()
+    res = (_D * n)()
+    status = (_I * n)()
+    _check(load().lbm_sweep_run_to_steady(s, float(tol), int(max_steps), int(check_every),
+                                          1 if autotune else 0, steps, res, status),
+           "lbm_sweep_run_to_steady")
+    return list(steps), list(res), list(status)
+
+
+def lbm_sweep_instance(s, k: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().lbm_sweep_instance(s, int(k), ctypes.byref(h)), "lbm_sweep_instance")
+    return h
+
+
+def lbm_sweep_schedule(s, n: int):
+    pol = _I()
+    rows = (_I * n)()
+    ms = (_D * LBM_SWEEP_NPOLICY)()
+    _check(load().lbm_sweep_schedule(s, ctypes.byref(pol), rows, ms), "lbm_sweep_schedule")
+    return pol.value, list(rows), list(ms)
+
+
 class LbmMix:
     """Owns one handle; methods forward to the same-name C functions."""
 
     def __init__(self, stream=None, **params):
         self.params = make_params(**params)
         self.h = lbm_mix_create(self.params, stream)
+        self._owned = True
         self.N, self.N_x, _ = lbm_mix_dims(self.h)
+
+    @classmethod
+    def borrowed(cls, h, params: lbm_mix_params):
+        """A view of a handle owned elsewhere (a sweep instance); never
+        destroys it."""
+        self = cls.__new__(cls)
+        self.params = params
+        self.h = h
+        self._owned = False
+        self.N, self.N_x, _ = lbm_mix_dims(self.h)
+        return self
 
     def close(self):
         if getattr(self, "h", None):
-            lbm_mix_destroy(self.h)
+            if getattr(self, "_owned", True):
+                lbm_mix_destroy(self.h)
             self.h = None
+
+    def set_rows_per_block(self, rows: int):
+        lbm_mix_set_rows_per_block(self.h, rows)
 
     def __del__(self):
         try:
@@ -346,3 +423,45 @@ class LbmMix:
 
     def run_to_steady(self, tol: float, max_steps: int, check_every: int = 100):
         return lbm_mix_run_to_steady(self.h, tol, max_steps, check_every)
+
+
+class LbmSweep:
+    """Owns a sweep of independent channels (one parameter dict each)."""
+
+    def __init__(self, params_list):
+        self.params = [make_params(**p) for p in params_list]
+        self.n = len(self.params)
+        self.s = lbm_sweep_create(self.params)
+        self._views = [None] * self.n
+
+    def close(self):
+        if getattr(self, "s", None):
+            self._views = []
+            lbm_sweep_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self):
+        lbm_sweep_init(self.s)
+
+    def step(self, n: int):
+        lbm_sweep_step(self.s, n)
+
+    def run_to_steady(self, tol: float, max_steps: int, check_every: int = 1000,
+                      autotune: bool = False):
+        """Per-instance (steps, residual, status) lists."""
+        return lbm_sweep_run_to_steady(self.s, self.n, tol, max_steps, check_every, autotune)
+
+    def instance(self, k: int) -> LbmMix:
+        if self._views[k] is None:
+            self._views[k] = LbmMix.borrowed(lbm_sweep_instance(self.s, k), self.params[k])
+        return self._views[k]
+
+    def schedule(self):
+        """(policy, rows per CTA of each instance, autotuner block times in ms)."""
+        return lbm_sweep_schedule(self.s, self.n)

@@ -31,6 +31,7 @@
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <time.h>
 #include <string.h>
 
 #include <mutex>
@@ -1201,6 +1202,7 @@ struct lbm_mix {
   double* colpart;     // [R][4][Nx]
   unsigned* strip_cnt; // [nblocks]
   int R, rows_per_block;
+  int R_alloc;        // row blocks colpart has room for
   double* resid;
   double* mom;
   double* h_pinned;  // small pinned staging area
@@ -1360,6 +1362,41 @@ int rereference(lbm_mix* h) {
   float* t = h->refrho;
   h->refrho = h->refrho_alt;
   h->refrho_alt = t;
+  return LBM_OK;
+}
+
+// Steady-state residual of the last k steps (Sec. 4 convergence check, over
+// the column sums of the latest DIAG step) into h->h_pinned[0], async.
+int launch_residual(lbm_mix* h, long k) {
+  lbm_residual_kernel<<<1, 1024, 0, h->stream>>>(h->cs[h->cur], h->cs_snap, 4L * h->L.Nx,
+                                                 (double)k, h->have_snap ? 1 : 0, h->resid);
+  CK(cudaGetLastError());
+  h->have_snap = true;
+  CK(cudaMemcpyAsync(h->h_pinned, h->resid, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return LBM_OK;
+}
+
+// Node-to-CTA schedule: rows per CTA (a multiple of TY); the per-row-block
+// partials grow when a schedule needs more row blocks than allocated.
+int set_rows_per_block(lbm_mix* h, int rows) {
+  const int nmax = (h->L.N + TY - 1) / TY * TY;
+  if (rows <= 0) {
+    const int R = (h->L.N + 127) / 128;
+    rows = ((h->L.N + R - 1) / R + TY - 1) / TY * TY;
+  }
+  if (rows % TY != 0) return set_err(LBM_EINVAL, "rows per block must be a multiple of %d", TY);
+  if (rows > nmax) rows = nmax;
+  const int R = (h->L.N + rows - 1) / rows;
+  if (R > h->R_alloc) {
+    double* cp = nullptr;
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMalloc((void**)&cp, sizeof(double) * 4 * (size_t)h->L.Nx * (size_t)R));
+    cudaFree(h->colpart);
+    h->colpart = cp;
+    h->R_alloc = R;
+  }
+  h->rows_per_block = rows;
+  h->R = R;
   return LBM_OK;
 }
 
@@ -1628,6 +1665,7 @@ int lbm_mix_create(const lbm_mix_params* p, void* stream, lbm_mix** out) {
   h->R = (h->L.N + 127) / 128;
   h->rows_per_block = ((h->L.N + h->R - 1) / h->R + TY - 1) / TY * TY;
   h->R = (h->L.N + h->rows_per_block - 1) / h->rows_per_block;
+  h->R_alloc = h->R;
   ALLOC(h->colpart, sizeof(double) * 4 * (size_t)Nx * (size_t)h->R);
   ALLOC(h->strip_cnt, sizeof(unsigned) * (size_t)h->nblocks);
   ALLOC(h->resid, sizeof(double));
@@ -1727,17 +1765,12 @@ int lbm_mix_run_to_steady(lbm_mix* h, double tol, long max_steps, long check_eve
     return set_err(LBM_EINVAL, "need tol > 0, max_steps >= 0, check_every >= 1");
   long taken = 0;
   double R = INFINITY;
-  const long n = 4L * h->L.Nx;
   int result = LBM_ENOTCONVERGED;
   while (taken < max_steps) {
     long k = check_every < max_steps - taken ? check_every : max_steps - taken;
     if ((st = lbm_mix_step(h, k))) return st;
     taken += k;
-    lbm_residual_kernel<<<1, 1024, 0, h->stream>>>(h->cs[h->cur], h->cs_snap, n, (double)k,
-                                                   h->have_snap ? 1 : 0, h->resid);
-    CK(cudaGetLastError());
-    h->have_snap = true;
-    CK(cudaMemcpyAsync(h->h_pinned, h->resid, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if ((st = launch_residual(h, k))) return st;
     CK(cudaStreamSynchronize(h->stream));
     R = h->h_pinned[0];
     if (isnan(R)) {
@@ -1754,6 +1787,12 @@ int lbm_mix_run_to_steady(lbm_mix* h, double tol, long max_steps, long check_eve
   if (result == LBM_ENOTCONVERGED)
     set_err(LBM_ENOTCONVERGED, "residual %.3e above %.3e after %ld steps", R, tol, taken);
   return result;
+}
+
+int lbm_mix_set_rows_per_block(lbm_mix* h, int rows) {
+  int st = check_handle(h);
+  if (st) return st;
+  return set_rows_per_block(h, rows);
 }
 
 int lbm_mix_moments_device(lbm_mix* h, double* d_out) {
@@ -1955,6 +1994,278 @@ int lbm_mix_step_noalloc(const lbm_mix_params* p, const float* d_in, float* d_ou
   dim3 blk(TX, TY), grd(nstrips, 1);
   lbm_step_kernel<float, true><<<grd, blk, 0, s>>>(L, a);
   CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- sweeps
+// A parametric study (Table 1) runs many independent channels.  Each
+// instance keeps its own handle and stream; K steps of an instance are
+// captured once as a CUDA graph (K fused step launches) and replayed, so the
+// host issues one graph launch per instance per convergence check and the
+// instances' kernels run concurrently, filling the GPU with channels that
+// are each too small to fill it alone.  The first blocks of
+// lbm_sweep_run_to_steady can serve as an autotuner of the node-to-CTA
+// schedule (rows per CTA): each candidate schedule runs one real block of
+// steps, the fastest is kept.  Schedules change only the order of the FP64
+// column reductions, not the time integration.
+struct lbm_sweep {
+  int n = 0;
+  lbm_mix** h = nullptr;
+  cudaGraphExec_t* exec = nullptr;
+  long* exec_K = nullptr;  // steps captured in exec[i]; 0 = none
+  int policy = -1;         // schedule in use (-1: the library default)
+  double round_ms[LBM_SWEEP_NPOLICY] = {};
+};
+
+namespace {
+
+// Rows per CTA of instance h under schedule policy p.
+int policy_rows(const lbm_mix* h, int p) {
+  const int N = h->L.N;
+  switch (p) {
+    case 0: return 0;  // library default: row blocks of <= 128 rows
+    case 1: return 64;
+    case 2: return 32;
+    case 3: return 16;
+    default: {  // fill: about two CTAs per SM for this instance alone
+      const long want = 2L * 152;
+      long rows = ((long)N * h->nblocks + want - 1) / want;
+      rows = (rows + TY - 1) / TY * TY;
+      if (rows < 16) rows = 16;
+      if (rows > 128) rows = 128;
+      return (int)rows;
+    }
+  }
+}
+
+void drop_graph(lbm_sweep* s, int i) {
+  if (s->exec[i]) cudaGraphExecDestroy(s->exec[i]);
+  s->exec[i] = nullptr;
+  s->exec_K[i] = 0;
+}
+
+// K (even) steps of instance i as one graph executable.  Capturing records
+// the launches without running them, so the host-side step count and buffer
+// parity are restored afterwards.
+int capture_steps(lbm_sweep* s, int i, long K) {
+  lbm_mix* h = s->h[i];
+  drop_graph(s, i);
+  const long steps0 = h->steps;
+  const int cur0 = h->cur;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  int st = lbm_mix_step(h, K);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  h->steps = steps0;
+  h->cur = cur0;
+  if (st) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess)
+    return set_err(LBM_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&s->exec[i], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    s->exec[i] = nullptr;
+    return set_err(LBM_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+  }
+  s->exec_K[i] = K;
+  return LBM_OK;
+}
+
+int apply_policy(lbm_sweep* s, int p) {
+  for (int i = 0; i < s->n; ++i) {
+    lbm_mix* h = s->h[i];
+    const int before = h->rows_per_block;
+    int st = set_rows_per_block(h, policy_rows(h, p));
+    if (st) return st;
+    if (h->rows_per_block != before) drop_graph(s, i);
+  }
+  s->policy = p;
+  return LBM_OK;
+}
+
+double now_ms() {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return ts.tv_sec * 1e3 + ts.tv_nsec * 1e-6;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_sweep_create(const lbm_mix_params* params, int n, lbm_sweep** out) {
+  if (!out) return set_err(LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!params || n < 1) return set_err(LBM_EINVAL, "need n >= 1 parameter sets");
+  for (int i = 0; i < n; ++i) {
+    int Nx = 0;
+    int st = validate(&params[i], &Nx);
+    if (st) {
+      char why[sizeof g_err];
+      memcpy(why, g_err, sizeof why);
+      return set_err(st, "instance %d: %s", i, why);
+    }
+    if (params[i].storage != LBM_FP32)
+      return set_err(LBM_EINVAL, "instance %d: sweeps run FP32 storage only", i);
+  }
+  lbm_sweep* s = new (std::nothrow) lbm_sweep;
+  if (!s) return set_err(LBM_ENOMEM, "host allocation failed");
+  s->h = (lbm_mix**)calloc(n, sizeof(lbm_mix*));
+  s->exec = (cudaGraphExec_t*)calloc(n, sizeof(cudaGraphExec_t));
+  s->exec_K = (long*)calloc(n, sizeof(long));
+  if (!s->h || !s->exec || !s->exec_K) {
+    lbm_sweep_destroy(s);
+    return set_err(LBM_ENOMEM, "host allocation failed");
+  }
+  s->n = n;
+  for (int i = 0; i < n; ++i) {
+    lbm_mix_params p = params[i];
+    p.reref_every = 0;
+    int st = lbm_mix_create(&p, nullptr, &s->h[i]);  // own stream per instance
+    if (st) {
+      lbm_sweep_destroy(s);
+      return st;
+    }
+  }
+  *out = s;
+  return LBM_OK;
+}
+
+void lbm_sweep_destroy(lbm_sweep* s) {
+  if (!s) return;
+  for (int i = 0; i < s->n; ++i) {
+    if (s->exec) drop_graph(s, i);
+    if (s->h) lbm_mix_destroy(s->h[i]);
+  }
+  free(s->h);
+  free(s->exec);
+  free(s->exec_K);
+  delete s;
+}
+
+int lbm_sweep_init(lbm_sweep* s) {
+  if (!s) return set_err(LBM_EINVAL, "sweep is NULL");
+  for (int i = 0; i < s->n; ++i) {
+    int st = lbm_mix_init(s->h[i]);
+    if (st) return st;
+  }
+  return LBM_OK;
+}
+
+int lbm_sweep_step(lbm_sweep* s, long nsteps) {
+  if (!s) return set_err(LBM_EINVAL, "sweep is NULL");
+  if (nsteps < 0) return set_err(LBM_EINVAL, "nsteps < 0");
+  for (int i = 0; i < s->n; ++i) {
+    int st = lbm_mix_step(s->h[i], nsteps);
+    if (st) return st;
+  }
+  for (int i = 0; i < s->n; ++i) CK(cudaStreamSynchronize(s->h[i]->stream));
+  return LBM_OK;
+}
+
+int lbm_sweep_run_to_steady(lbm_sweep* s, double tol, long max_steps, long check_every,
+                            int autotune, long* steps_out, double* residual_out,
+                            int* status_out) {
+  if (!s) return set_err(LBM_EINVAL, "sweep is NULL");
+  if (!(tol > 0) || max_steps < 0 || check_every < 2 || check_every % 2 != 0)
+    return set_err(LBM_EINVAL, "need tol > 0, max_steps >= 0, even check_every >= 2");
+  const int n = s->n;
+  long* taken = (long*)calloc(n, sizeof(long));
+  double* R = (double*)malloc(n * sizeof(double));
+  int* status = (int*)malloc(n * sizeof(int));
+  int* act = (int*)malloc(n * sizeof(int));
+  if (!taken || !R || !status || !act) {
+    free(taken), free(R), free(status), free(act);
+    return set_err(LBM_ENOMEM, "host allocation failed");
+  }
+  int na = 0;
+  for (int i = 0; i < n; ++i) {
+    R[i] = INFINITY;
+    status[i] = LBM_ENOTCONVERGED;
+    // one diagnostic record per graph: the captured pattern repeats
+    s->h[i]->p.diag_every = (int)check_every;
+    if (max_steps > 0) act[na++] = i;
+  }
+  int st = LBM_OK;
+  int trial = autotune ? 0 : -1;  // next schedule to try
+  if (!autotune && s->policy < 0) st = apply_policy(s, 0);
+  while (na > 0 && st == LBM_OK) {
+    if (trial >= 0 && (st = apply_policy(s, trial))) break;
+    // every active instance advances k steps: a replayed graph when k is
+    // the captured length, plain launches for a shorter last block
+    const long left = max_steps - taken[act[0]];
+    const long k = check_every < left ? check_every : left;
+    for (int a = 0; a < na && !st; ++a)
+      if (k == check_every && s->exec_K[act[a]] != k) st = capture_steps(s, act[a], k);
+    if (st) break;
+    const double t0 = now_ms();
+    for (int a = 0; a < na && !st; ++a) {
+      lbm_mix* h = s->h[act[a]];
+      if (k == check_every) {
+        cudaError_t e = cudaGraphLaunch(s->exec[act[a]], h->stream);
+        if (e != cudaSuccess) st = set_err(LBM_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+        h->steps += k;
+      } else {
+        st = lbm_mix_step(h, k);
+      }
+      if (!st) st = launch_residual(h, k);
+    }
+    if (st) break;
+    int nb = 0;
+    for (int a = 0; a < na; ++a) {
+      const int i = act[a];
+      lbm_mix* h = s->h[i];
+      cudaError_t e = cudaStreamSynchronize(h->stream);
+      if (e != cudaSuccess) {
+        st = set_err(LBM_ECUDA, "instance %d: %s", i, cudaGetErrorString(e));
+        break;
+      }
+      taken[i] += k;
+      R[i] = h->h_pinned[0];
+      if (isnan(R[i])) status[i] = LBM_ENONFINITE;
+      else if (R[i] <= tol) status[i] = LBM_OK;
+      else if (taken[i] < max_steps) act[nb++] = i;
+    }
+    if (st) break;
+    if (trial >= 0) {
+      s->round_ms[trial] = now_ms() - t0;
+      if (++trial == LBM_SWEEP_NPOLICY) {
+        int best = 0;
+        for (int p = 1; p < LBM_SWEEP_NPOLICY; ++p)
+          if (s->round_ms[p] < s->round_ms[best]) best = p;
+        trial = -1;
+        st = apply_policy(s, best);
+      }
+    }
+    na = nb;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (steps_out) steps_out[i] = taken[i];
+    if (residual_out) residual_out[i] = R[i];
+    if (status_out) status_out[i] = status[i];
+  }
+  free(taken), free(R), free(status), free(act);
+  return st;
+}
+
+int lbm_sweep_instance(lbm_sweep* s, int k, lbm_mix** out) {
+  if (!s || !out || k < 0 || k >= s->n) return set_err(LBM_EINVAL, "bad sweep, index or out");
+  *out = s->h[k];
+  return LBM_OK;
+}
+
+int lbm_sweep_schedule(lbm_sweep* s, int* policy, int* rows_per_block, double* round_ms) {
+  if (!s) return set_err(LBM_EINVAL, "sweep is NULL");
+  if (policy) *policy = s->policy;
+  if (rows_per_block)
+    for (int i = 0; i < s->n; ++i) rows_per_block[i] = s->h[i]->rows_per_block;
+  if (round_ms)
+    for (int p = 0; p < LBM_SWEEP_NPOLICY; ++p) round_ms[p] = s->round_ms[p];
   return LBM_OK;
 }
 

@@ -69,3 +69,23 @@ def random_accommodation(N_x: int, seed: int, spread: float = 0.05) -> np.ndarra
     1 - U(0, spread) so that it stays in (0, 1]."""
     rng = np.random.default_rng(seed)
     return 1.0 - rng.uniform(0.0, spread, size=2 * N_x)
+
+
+def sweep_instances(n: int = 96, seed: int = 0) -> list[dict]:
+    """A parametric study in the spirit of Table 1 (gas pair, inlet
+    composition, pressure ratio, Knudsen number, channel size), drawn with
+    numpy's PCG64 from `seed`: He-Ar and Ne-Ar alternate, C_l cycles through
+    0.1, 0.3, 0.5, 0.7, 0.9, theta ~ U[1.5, 5], Kn_out = 10^U[-2, 0],
+    N from {16, 32, 64, 128} and L/H from {10, 20, 50}.  The draws are made
+    in that order per instance."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for k in range(n):
+        theta = float(rng.uniform(1.5, 5.0))
+        kn = float(10.0 ** rng.uniform(-2.0, 0.0))
+        N = int(rng.choice([16, 32, 64, 128]))
+        LH = float(rng.choice([10.0, 20.0, 50.0]))
+        out.append(dict(m_a=HE if k % 2 == 0 else NE, m_b=AR,
+                        C_l=(0.1, 0.3, 0.5, 0.7, 0.9)[k % 5], theta=theta, Kn_out=kn,
+                        N=N, L_over_H=LH))
+    return out

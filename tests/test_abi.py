@@ -97,3 +97,19 @@ def test_missing_library_fails_loudly(tmp_path):
             binding.load(str(tmp_path / "nope.so"))
         finally:
             binding._lib = binding._lib_backup
+
+
+def test_sweep_rejects_bad_instances_without_gpu(lib):
+    good = binding.lbm_mix_default_params()
+    bad = binding.lbm_mix_default_params()
+    bad.theta = 0.5
+    low = binding.lbm_mix_default_params()
+    low.storage = binding.LBM_BF16
+    for plist in ([good, bad], [low]):
+        arr = (binding.lbm_mix_params * len(plist))(*plist)
+        s = ctypes.c_void_p()
+        assert lib.lbm_sweep_create(arr, len(plist), ctypes.byref(s)) == binding.LBM_EINVAL
+        assert s.value is None
+    assert "instance 1" in binding.lbm_mix_last_error() or "FP32" in binding.lbm_mix_last_error()
+    s = ctypes.c_void_p()
+    assert lib.lbm_sweep_create(None, 0, ctypes.byref(s)) == binding.LBM_EINVAL
