@@ -33,6 +33,7 @@ REF_SAMPLE = "neon_argon_2048x32"  # 1/16 linear-scale copy (same C_l, theta, Kn
 KERNEL = "lbm_step_kernel"
 PROFILE_MD = os.path.join(ROOT, "profiles", "lbm_step_kernel_neon_argon_32768x512.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_1603_08221_gb300", "csrc", "lbm_mix.cu")
+KERNEL_SECTION_END = b"// ------------------------------------------------------------ init kernels"
 
 
 def dist_env():
@@ -118,8 +119,18 @@ def profiled_traffic():
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
     if not m or not h:
         return None
-    cur = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
-    return float(m.group(1)) if h.group(1) == cur else None
+    return float(m.group(1)) if h.group(1) == kernel_source_sha256() else None
+
+
+def kernel_source_sha256():
+    """sha256 of the device-code part of the library source that the step
+    kernel is built from (everything before the init kernels); host-side
+    changes below that point leave the recorded counters valid."""
+    text = open(KERNEL_SRC, "rb").read()
+    end = text.find(KERNEL_SECTION_END)
+    if end < 0:
+        raise RuntimeError(f"marker {KERNEL_SECTION_END!r} missing from {KERNEL_SRC}")
+    return hashlib.sha256(text[:end]).hexdigest()
 
 
 def oracle_throughput(steps: int, sample: str):
@@ -136,6 +147,58 @@ def oracle_throughput(steps: int, sample: str):
     dt = time.perf_counter() - t0
     nodes = o.N * (o.N_x - 2)
     return nodes * steps / dt / 1e6, dt, oracle.num_threads(), nodes
+
+
+def run_sweep(args, rank, world, barrier):
+    """The seeded 96-channel parametric study run to a residual of 1e-8 (or
+    the step cap): once as a graph-replayed concurrent sweep with the
+    schedule autotuner, once as sequential lone runs (plain launches).
+    Instances are dealt round-robin over the ranks."""
+    from paper_1603_08221_gb300 import binding, workloads
+    inst = workloads.sweep_instances()
+    mine = [p for k, p in enumerate(inst) if k % world == rank]
+    tol, check = 1e-8, 1000
+    sw = binding.LbmSweep(mine)
+    sw.init()
+    barrier()
+    t0 = time.perf_counter()
+    steps, _, status = sw.run_to_steady(tol, args.sweep_cap, check, autotune=True)
+    barrier()
+    t_sweep = time.perf_counter() - t0
+    policy, _, round_ms = sw.schedule()
+    sw.close()
+    t0 = time.perf_counter()
+    for k, p in enumerate(mine):
+        g = binding.LbmMix(**p)
+        g.init()
+        try:
+            g.run_to_steady(tol, args.sweep_cap, check)
+        except binding.LbmError as e:
+            if e.status != binding.LBM_ENONFINITE:
+                raise
+        g.close()
+    barrier()
+    t_seq = time.perf_counter() - t0
+    solved = sum(1 for st in status if st == binding.LBM_OK)
+    updates = sum(p["N"] * (workloads.n_x(p) - 2) * n for p, n in zip(mine, steps))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([t_sweep, t_seq], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        c = torch.tensor([solved, updates], dtype=torch.float64, device="cuda")
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        t_sweep, t_seq = float(t[0]), float(t[1])
+        solved, updates = int(c[0]), int(c[1])
+    return {"instances": len(inst), "tol": tol, "check_every": check,
+            "step_cap": args.sweep_cap, "solves": solved, "seconds": t_sweep,
+            "solves_per_s": solved / t_sweep, "sequential_seconds": t_seq,
+            "sequential_solves_per_s": solved / t_seq, "speedup": t_seq / t_sweep,
+            "aggregate_mlups": updates / t_sweep / 1e6,
+            "outcomes": {"converged": status.count(binding.LBM_OK),
+                         "step_cap": status.count(binding.LBM_ENOTCONVERGED),
+                         "diverged": status.count(binding.LBM_ENONFINITE)},
+            "autotuned_policy": policy, "autotune_block_ms": round_ms}
 
 
 def run_reference(args):
@@ -254,6 +317,8 @@ def run_ours(args):
                               "reref_every": 256}
             del v
 
+    sweep = None if args.no_sweep else run_sweep(args, rank, world, barrier)
+
     # ---------------- whole-job aggregation (max time over ranks)
     if world > 1:
         import torch.distributed as dist
@@ -295,6 +360,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h / args.steps},
         "gpu_launches": args.steps,
         "storage_variants": variants or None,
+        "sweep": sweep,
         "clocks": clk.summary(),
         "result": {"CL": sep["CL"], "Cl_tilde": sep["Cl_tilde"], "mdot_a": sep["mdot_a"],
                    "mdot_b": sep["mdot_b"], "CL_e2e_run": sep_e2e["CL"]},
@@ -319,6 +385,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the BF16/FP16 storage timings")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the 96-channel parametric sweep")
+    ap.add_argument("--sweep-cap", type=int, default=10000,
+                    help="step cap per sweep instance (200000 for the full study)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
