@@ -256,3 +256,16 @@ def test_paper_trend_mass_ratio(orc):
         assert s["CL"] > 0 and s["Cl_profile"][1:-1].min() < 0.5
         assert 1 <= s["x_min"] <= len(s["Cl_profile"]) - 2
     assert ne["CL"] < he["CL"]
+
+
+def test_oracle_diverges_where_the_sweep_diverges(orc):
+    """Sweep instance 42 (N = 16, 160 columns, theta = 4.6, Kn_out = 0.028)
+    drives the scheme unstable: relaxation times near 1/2 and a large
+    pressure drop.  The FP64 oracle blows up on it too (non-finite within
+    1000 steps), so a diverged sweep instance is the method's, not the
+    kernel's."""
+    p = workloads.sweep_instances()[42]
+    o = orc.Oracle(p)
+    o.init()
+    o.step(1000)
+    assert not np.isfinite(o.moments()["rho_a"]).all()

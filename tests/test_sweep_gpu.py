@@ -111,3 +111,13 @@ def test_rows_per_block_changes_only_reduction_order(rows):
     for key in ("ua_x", "ub_x"):
         assert np.abs(m[key] - mr[key]).max() < 10 * RTOL_SCHED * scale, key
     assert abs(g.separation()["CL"] - ref.separation()["CL"]) < 1e-6
+
+
+def test_sweep_reports_a_diverging_instance():
+    """An unstable instance stops with LBM_ENONFINITE; the others go on."""
+    unstable = workloads.sweep_instances()[42]
+    sw = binding.LbmSweep([unstable, SMALL[0]])
+    sw.init()
+    steps, R, status = sw.run_to_steady(1e-7, 40000, 500)
+    assert status[0] == binding.LBM_ENONFINITE and steps[0] <= 2000
+    assert status[1] == binding.LBM_OK
