@@ -298,6 +298,57 @@ int lbm_sweep_instance(lbm_sweep* s, int k, lbm_mix** out);
  * not measured).  All outputs nullable. */
 int lbm_sweep_schedule(lbm_sweep* s, int* policy, int* rows_per_block, double* round_ms);
 
+/* ---------------------------------------------------------------------
+ * Adjoint (gradients of a steady-channel objective).  A handle runs the
+ * time step in FP64 on the full populations (the same map as lbm_mix_step:
+ * Sec. 3 with the readings of this library) for nsteps steps from the
+ * initial state of lbm_mix_init, keeping a checkpoint every
+ * checkpoint_every steps, and computes the discrete adjoint of that run:
+ * one backward sweep replays each checkpoint interval and runs the reverse
+ * of each step (collision, tau_q at the walls, streaming with the DBB rule
+ * of Eqs. bot, bot2, R and the ends of Eqs. rho1, rho2).  Gradients are
+ * exact for the FP64 map up to rounding.  No counterpart in the paper (it
+ * reports no sensitivities).
+ * ------------------------------------------------------------------- */
+typedef struct lbm_adj lbm_adj;
+
+/* Objectives, both of the state after the last step:
+ *   LBM_ADJ_CL    CL = (C_l,in - min_x C_l(x)) / C_l,in over the updated
+ *                 columns, C_l(x) = sum_j n_l / sum_j n (Eq. CL; the
+ *                 gradient flows through the minimising column);
+ *   LBM_ADJ_FLUX  light-species x momentum summed over column N_x - 2 (the
+ *                 outlet mass flux of the light species). */
+#define LBM_ADJ_CL 0
+#define LBM_ADJ_FLUX 1
+
+/* Validates p like lbm_mix_create (storage is ignored: FP64) and allocates
+ * the checkpoints (ceil(nsteps/checkpoint_every) + 1 states of 18 N N_x
+ * doubles) and one interval of replayed states.  stream: cudaStream_t or
+ * NULL for an own stream.  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
+int lbm_adj_create(const lbm_mix_params* p, long nsteps, int checkpoint_every, void* stream,
+                   lbm_adj** out);
+
+/* Releases the handle.  NULL-safe. */
+void lbm_adj_destroy(lbm_adj* a);
+
+/* Per-wall-node accommodation coefficients alpha (Eq. A12 and c_m of
+ * Eq. R), host array [2][N_x] (bottom wall then top), each in (0, 1]. */
+int lbm_adj_set_accommodation_field(lbm_adj* a, const double* alpha, long n);
+
+/* Runs the forward steps; CL and flux (nullable) receive both objectives.
+ * LBM_ENONFINITE if the run diverged. */
+int lbm_adj_forward(lbm_adj* a, double* CL, double* flux);
+
+/* The FP64 state after the forward run, host [2][9][N][N_x]. */
+int lbm_adj_state(lbm_adj* a, double* f, long n);
+
+/* Backward sweep for `objective` after lbm_adj_forward: dJ/dtheta,
+ * dJ/dKn_out and dJ/dalpha (host [2][N_x], n_alpha = 2 N_x); outputs
+ * nullable.  theta enters the inlet densities (Eq. rho2) and the initial
+ * state, Kn_out the viscosity that sets every mean free path. */
+int lbm_adj_gradient(lbm_adj* a, int objective, double* dtheta, double* dkn, double* dalpha,
+                     long n_alpha);
+
 /* Static description of an error code; never NULL. */
 const char* lbm_mix_strerror(int status);
 

@@ -90,6 +90,13 @@ _SIGS = {
                                      ctypes.POINTER(_I)]),
     "lbm_sweep_instance": (_I, [_H, _I, ctypes.POINTER(ctypes.c_void_p)]),
     "lbm_sweep_schedule": (_I, [_H, ctypes.POINTER(_I), ctypes.POINTER(_I), _PD]),
+    "lbm_adj_create": (_I, [ctypes.POINTER(lbm_mix_params), _L, _I, ctypes.c_void_p,
+                            ctypes.POINTER(ctypes.c_void_p)]),
+    "lbm_adj_destroy": (None, [_H]),
+    "lbm_adj_set_accommodation_field": (_I, [_H, _PD, _L]),
+    "lbm_adj_forward": (_I, [_H, _PD, _PD]),
+    "lbm_adj_state": (_I, [_H, _PD, _L]),
+    "lbm_adj_gradient": (_I, [_H, _I, _PD, _PD, _PD, _L]),
     "lbm_mix_strerror": (ctypes.c_char_p, [_I]),
     "lbm_mix_last_error": (ctypes.c_char_p, []),
 }
@@ -465,3 +472,60 @@ class LbmSweep:
     def schedule(self):
         """(policy, rows per CTA of each instance, autotuner block times in ms)."""
         return lbm_sweep_schedule(self.s, self.n)
+
+
+LBM_ADJ_CL = 0
+LBM_ADJ_FLUX = 1
+
+
+class LbmAdjoint:
+    """FP64 forward run of nsteps steps with checkpoints and its discrete
+    adjoint (lbm_adj_* of the C ABI).  ``alpha``: optional [2][N_x]
+    accommodation field (bottom wall, then top)."""
+
+    def __init__(self, params: dict, nsteps: int, checkpoint_every: int = 70, alpha=None,
+                 stream=None):
+        self.params = make_params(**params)
+        lib = load()
+        h = ctypes.c_void_p()
+        st = lib.lbm_adj_create(ctypes.byref(self.params), int(nsteps), int(checkpoint_every),
+                                _stream_handle(stream), ctypes.byref(h))
+        _check(st, "lbm_adj_create")
+        self.h = h
+        self.N = self.params.N
+        self.N_x = self.params.N_x if self.params.N_x > 0 else int(
+            round(self.params.N * self.params.L_over_H))
+        if alpha is not None:
+            a = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64).ravel())
+            _check(lib.lbm_adj_set_accommodation_field(self.h, _dptr(a), a.size),
+                   "lbm_adj_set_accommodation_field")
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbm_adj_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self):
+        """Runs the steps; returns (CL, light-species outlet flux)."""
+        cl, fl = _D(), _D()
+        _check(load().lbm_adj_forward(self.h, ctypes.byref(cl), ctypes.byref(fl)),
+               "lbm_adj_forward")
+        return cl.value, fl.value
+
+    def state(self) -> np.ndarray:
+        f = np.empty((2, 9, self.N, self.N_x), dtype=np.float64)
+        _check(load().lbm_adj_state(self.h, _dptr(f), f.size), "lbm_adj_state")
+        return f
+
+    def gradient(self, objective: int = LBM_ADJ_CL) -> dict:
+        th, kn = _D(), _D()
+        da = np.empty(2 * self.N_x, dtype=np.float64)
+        _check(load().lbm_adj_gradient(self.h, int(objective), ctypes.byref(th), ctypes.byref(kn),
+                                       _dptr(da), da.size), "lbm_adj_gradient")
+        return {"theta": th.value, "Kn_out": kn.value, "alpha": da.reshape(2, self.N_x)}

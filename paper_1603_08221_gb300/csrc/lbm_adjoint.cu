@@ -1,0 +1,1128 @@
+// lbm_adjoint.cu — FP64 forward replay and discrete adjoint of the
+// two-species MRT-LBM time step (sm_103a), behind the lbm_adj_* entry points
+// of include/lbm_mix.h.
+//
+// The forward map here is the same time step as lbm_step_kernel (Sec. 3:
+// pull-streaming with the diffuse-bounce-back walls of Eqs. bot, bot2, R and
+// the extrapolation-correction ends of Eqs. rho1, rho2, moments of
+// Eq. rhou, effective relaxation times of Eqs. EQFrb, EQFrsp, psi, taos,
+// taoq, A12, and the MRT collision of Eqs. MR, m, S, feq), written in FP64
+// on the full populations in a plain [species][i][row][column] layout.  It
+// is the map the adjoint differentiates, so the gradient is exact for it
+// (up to FP64 rounding).
+//
+// One step t maps the post-collision state f^{t-1} to f^t through
+//   r(x, wall)  = R(alpha, m_x of f^{t-1} at the wall node)        per column
+//   kappa_s     = N rho_s,in / sum_j (2 rho_s(1, j) - rho_s(2, j)) per end
+//   g           = Pull(f^{t-1}; r, kappa)                          per node
+//   tau_q(x, w) = TQ(moments of g at the wall node, alpha)         per column
+//   f^t         = Collide(g; tau_q of the node's half, y)          per node
+// and the adjoint step runs these pieces backwards: the node-local reverse
+// of Collide (hand-derived, below), the reverse of TQ into the wall nodes'
+// g adjoints, the transpose of Pull as a gather over the nodes each
+// population was pulled by (with the DBB and ghost-column terms), and the
+// reverses of R and kappa.  Parameter adjoints: theta enters rho_in (kappa)
+// and the initial state; Kn_out scales mu and with it every mean free path
+// (accumulated as d/d ln mu); alpha enters R and TQ per wall node.
+//
+// All reductions are owned by one thread or one block in a fixed order, so
+// the gradient is deterministic.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "lbm_internal.h"
+
+#define CKA(call)                                                                       \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return lbm_internal_error(LBM_ECUDA, "%s failed: %s (%s:%d)", #call,               \
+                                cudaGetErrorString(e_), __FILE__, __LINE__);            \
+  } while (0)
+
+namespace {
+
+constexpr double kPiD = 3.14159265358979323846;
+constexpr double kEulerGamma = 0.57721566490153286061;
+__constant__ int CXd[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int CYd[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+// FP64 lattice constants of one problem.
+struct AL {
+  int N, Nx, x_periodic, light;
+  double s[2], mh[2], cw[2][3];  // rest weights w_i alpha_si: rest, axis, diagonal
+  double c_lam, c_xl[2], c_ts, c_td, om_e, om_eps, c_m0, H;
+  double rho_in[2], rho_out[2], C_in, C_out, theta;
+};
+
+// ------------------------------------------------ special functions (FP64)
+// 1/k for the series below (multiplications instead of FP64 divisions).
+__constant__ double kInvK[48] = {
+    0.0,       1.0,       1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,  1.0 / 7,
+    1.0 / 8,   1.0 / 9,   1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15,
+    1.0 / 16,  1.0 / 17,  1.0 / 18, 1.0 / 19, 1.0 / 20, 1.0 / 21, 1.0 / 22, 1.0 / 23,
+    1.0 / 24,  1.0 / 25,  1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29, 1.0 / 30, 1.0 / 31,
+    1.0 / 32,  1.0 / 33,  1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39,
+    1.0 / 40,  1.0 / 41,  1.0 / 42, 1.0 / 43, 1.0 / 44, 1.0 / 45, 1.0 / 46, 1.0 / 47};
+
+// E_1 from its power series for x <= 3 (A&S 5.1.11: at x = 3 the series'
+// cancellation costs ~2.5 digits, leaving ~4e-14 relative) and its continued
+// fraction for x > 3 (A&S 5.1.22, modified Lentz, which converges in a few
+// tens of terms there); both loops are bounded.
+__device__ double e1d(double x) {
+  if (x <= 3.0) {
+    double t = 1.0, s = 0.0;
+    for (int k = 1; k < 48; ++k) {
+      t *= -x * kInvK[k];
+      const double d = t * kInvK[k];
+      s += d;
+      if (fabs(d) < 1e-17 * fabs(s)) break;
+    }
+    return -kEulerGamma - log(x) - s;
+  }
+  const double tiny = 1e-300;
+  double b = x + 1.0, c = 1.0 / tiny, d = 1.0 / b, h = d;
+  for (int i = 1; i < 200; ++i) {
+    const double a = -(double)i * i;
+    b += 2.0;
+    d = 1.0 / (a * d + b);
+    c = b + a / c;
+    const double del = c * d;
+    h *= del;
+    if (fabs(del - 1.0) < 1e-16) break;
+  }
+  return h * exp(-x);
+}
+
+// psi(a) = 1 + (a - 1) e^{-a} - a^2 E_1(a) (Eq. psi), psi(0) = 0, and its
+// first two derivatives: psi' = 2 e^{-a} - 2 a E_1(a), psi'' = -2 E_1(a).
+struct Psi3 {
+  double v, d1, d2;
+};
+__device__ Psi3 psid(double a) {
+  Psi3 p;
+  if (!(a > 0.0)) {
+    p.v = 0.0;
+    p.d1 = 2.0;
+    p.d2 = -INFINITY;
+    return p;
+  }
+  const double e1 = e1d(a), ea = exp(-a);
+  p.v = 1.0 + (a - 1.0) * ea - a * a * e1;
+  p.d1 = 2.0 * ea - 2.0 * a * e1;
+  p.d2 = -2.0 * e1;
+  return p;
+}
+
+__device__ __forceinline__ size_t fidx(const AL& L, int sp, int i, int j, int x) {
+  return (((size_t)sp * 9 + i) * L.N + j) * L.Nx + x;
+}
+__device__ __forceinline__ bool interior(const AL& L, int x) {
+  return L.x_periodic ? (x >= 0 && x < L.Nx) : (x >= 1 && x <= L.Nx - 2);
+}
+__device__ __forceinline__ int wrapx(const AL& L, int x) {
+  if (!L.x_periodic) return x;
+  return x < 0 ? x + L.Nx : (x >= L.Nx ? x - L.Nx : x);
+}
+__device__ __forceinline__ double cwi(const AL& L, int sp, int i) {
+  return L.cw[sp][i == 0 ? 0 : (i < 5 ? 1 : 2)];
+}
+
+// Per-step column data: r of both walls per column, 1/tau_q of both halves
+// per column, kappa of both ends per species.
+struct StepCols {
+  double* r;      // [2][Nx] bottom, top
+  double* omq;    // [2][Nx]
+  double* kappa;  // [4]: in_a, in_b, out_a, out_b
+};
+
+// ----------------------------------------------------------------- pull
+// Source value of population i of species sp at (xs, js): the stored state,
+// or the virtual ghost column at an end (Eq. rho1, all nine extrapolated and
+// scaled by Eq. rho2's kappa).
+__device__ double src(const AL& L, const double* f, const double* kap, int sp, int i, int js,
+                      int xs) {
+  if (!L.x_periodic) {
+    if (xs == 0) return kap[sp] * (2.0 * f[fidx(L, sp, i, js, 1)] - f[fidx(L, sp, i, js, 2)]);
+    if (xs == L.Nx - 1)
+      return kap[2 + sp] *
+             (2.0 * f[fidx(L, sp, i, js, L.Nx - 2)] - f[fidx(L, sp, i, js, L.Nx - 3)]);
+  }
+  return f[fidx(L, sp, i, js, wrapx(L, xs))];
+}
+
+// f_i(x) = f'_i(x - c_i) with diffuse bounce-back at rows 0 and N-1: the
+// unknowns take (1 - r) of the opposite outgoing population plus r times the
+// wall equilibrium with zero normal species flux, 6 w_i (sum of outgoing).
+__device__ void pull(const AL& L, const double* f, const double* r2, const double* kap, int x,
+                     int j, double g[2][9]) {
+  const double rb = r2[x], rt = r2[L.Nx + x];
+  for (int sp = 0; sp < 2; ++sp) {
+    double* q = g[sp];
+    q[0] = f[fidx(L, sp, 0, j, x)];
+    q[1] = src(L, f, kap, sp, 1, j, x - 1);
+    q[3] = src(L, f, kap, sp, 3, j, x + 1);
+    if (j == 0) {
+      const double o4 = f[fidx(L, sp, 4, j, x)], o7 = f[fidx(L, sp, 7, j, x)],
+                   o8 = f[fidx(L, sp, 8, j, x)];
+      const double S = o4 + o7 + o8;
+      q[2] = (1.0 - rb) * o4 + rb * (2.0 / 3.0) * S;
+      q[5] = (1.0 - rb) * o7 + rb * S / 6.0;
+      q[6] = (1.0 - rb) * o8 + rb * S / 6.0;
+    } else {
+      q[2] = f[fidx(L, sp, 2, j - 1, x)];
+      q[5] = src(L, f, kap, sp, 5, j - 1, x - 1);
+      q[6] = src(L, f, kap, sp, 6, j - 1, x + 1);
+    }
+    if (j == L.N - 1) {
+      const double o2 = f[fidx(L, sp, 2, j, x)], o5 = f[fidx(L, sp, 5, j, x)],
+                   o6 = f[fidx(L, sp, 6, j, x)];
+      const double S = o2 + o5 + o6;
+      q[4] = (1.0 - rt) * o2 + rt * (2.0 / 3.0) * S;
+      q[7] = (1.0 - rt) * o5 + rt * S / 6.0;
+      q[8] = (1.0 - rt) * o6 + rt * S / 6.0;
+    } else {
+      q[4] = f[fidx(L, sp, 4, j + 1, x)];
+      q[7] = src(L, f, kap, sp, 7, j + 1, x + 1);
+      q[8] = src(L, f, kap, sp, 8, j + 1, x - 1);
+    }
+  }
+}
+
+// ------------------------------------------------ node collision (FP64)
+// Forward intermediates of one node, kept for the reverse pass.
+struct NodeFwd {
+  double rho[2], jx[2], jy[2], rho_t, ux, uy, n, mx;
+  double lam, Pm, dPm, tsm, om_s;     // mixture mean free path, Psi, dPsi/dlam, tau_s - 1/2, 1/tau_s
+  double lams[2], Ps[2], dPs[2], xle[2], br, d, om_d;
+  double m[2][9], meq[2][9];
+};
+
+// Rows of M in the order rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy
+// (Eq. m) and the diagonal of M M^T.
+__device__ __forceinline__ double Mki(int k, int i) {
+  const int cx = CXd[i], cy = CYd[i];
+  const int c2 = cx * cx + cy * cy;
+  switch (k) {
+    case 0: return 1.0;
+    case 1: return -4.0 + 3.0 * c2;
+    case 2: return 4.0 - 10.5 * c2 + 4.5 * c2 * c2;
+    case 3: return cx;
+    case 4: return (3.0 * c2 - 5.0) * cx;
+    case 5: return cy;
+    case 6: return (3.0 * c2 - 5.0) * cy;
+    case 7: return cx * cx - cy * cy;
+    default: return cx * cy;
+  }
+}
+__device__ __forceinline__ double Mnorm(int k) {
+  const double w[9] = {9.0, 36.0, 36.0, 6.0, 12.0, 6.0, 12.0, 4.0, 4.0};
+  return w[k];
+}
+
+__device__ double half_psi(double y, double H, double lam, double* dlam) {
+  const Psi3 a = psid(y / lam), b = psid((H - y) / lam);
+  if (dlam) *dlam = 0.5 * (a.d1 * (-y / (lam * lam)) + b.d1 * (-(H - y) / (lam * lam)));
+  return 0.5 * (a.v + b.v);
+}
+
+// f_out = Collide(g): moments, relaxation rates (1/tau_s of Eq. taos,
+// 1/tau_d of Eq. EQFrsp, 1/tau_q from the wall), MRT relaxation
+// f' = g - M^{-1} S (m - m^eq).
+__device__ void node_forward(const AL& L, const double g[2][9], double y, double omq,
+                             NodeFwd& F, double fo[2][9]) {
+  for (int sp = 0; sp < 2; ++sp) {
+    double r = 0, jx = 0, jy = 0;
+    for (int i = 0; i < 9; ++i) {
+      r += g[sp][i];
+      jx += CXd[i] * g[sp][i];
+      jy += CYd[i] * g[sp][i];
+    }
+    F.rho[sp] = r;
+    F.jx[sp] = jx;
+    F.jy[sp] = jy;
+  }
+  F.rho_t = F.rho[0] + F.rho[1];
+  F.ux = (F.jx[0] + F.jx[1]) / F.rho_t;
+  F.uy = (F.jy[0] + F.jy[1]) / F.rho_t;
+  F.n = L.s[0] * F.rho[0] + L.s[1] * F.rho[1];
+  F.mx = F.rho_t / F.n;
+  F.lam = L.c_lam / (F.n * sqrt(F.mx));
+  F.Pm = half_psi(y, L.H, F.lam, &F.dPm);
+  F.tsm = F.lam * F.Pm * L.c_ts / sqrt(F.mx);
+  F.om_s = 1.0 / (0.5 + F.tsm);
+  F.br = 0.0;
+  for (int sp = 0; sp < 2; ++sp) {
+    F.lams[sp] = L.c_xl[sp] / (L.s[sp] * F.rho[sp]);
+    F.Ps[sp] = half_psi(y, L.H, F.lams[sp], &F.dPs[sp]);
+    F.xle[sp] = L.c_xl[sp] * F.Ps[sp] / F.n;
+    F.br += 1.0 / sqrt(F.xle[sp]);
+  }
+  F.d = F.mx * F.br * F.br;
+  F.om_d = F.d / (0.5 * F.d + L.c_td);
+  const double u2 = F.ux * F.ux + F.uy * F.uy;
+  const double S[9] = {0.0, L.om_e, L.om_eps, F.om_d, omq, F.om_d, omq, F.om_s, F.om_s};
+  for (int sp = 0; sp < 2; ++sp) {
+    const double r = F.rho[sp], s = L.s[sp];
+    const double br[9] = {1.0, -4.0 + 2.0 * s + 3.0 * u2, 4.0 - 3.0 * s - 3.0 * u2, F.ux,
+                          -F.ux, F.uy, -F.uy, F.ux * F.ux - F.uy * F.uy, F.ux * F.uy};
+    double dl[9];
+    for (int k = 0; k < 9; ++k) {
+      double mk = 0;
+      for (int i = 0; i < 9; ++i) mk += Mki(k, i) * g[sp][i];
+      F.m[sp][k] = mk;
+      F.meq[sp][k] = r * br[k];
+      dl[k] = S[k] * (mk - F.meq[sp][k]) / Mnorm(k);
+    }
+    for (int i = 0; i < 9; ++i) {
+      double c = 0;
+      for (int k = 0; k < 9; ++k) c += Mki(k, i) * dl[k];
+      fo[sp][i] = g[sp][i] - c;
+    }
+  }
+}
+
+// Reverse of node_forward: from fbar (adjoint of f_out) to gbar (adjoint of
+// g), omq_bar (adjoint of 1/tau_q) and lnmu_bar (adjoint of ln mu, which
+// scales c_lam and c_xl).
+__device__ void node_reverse(const AL& L, const double g[2][9], double y, double omq,
+                             const double fbar[2][9], double gbar[2][9], double* omq_bar,
+                             double* lnmu_bar) {
+  NodeFwd F;
+  double fo[2][9];
+  node_forward(L, g, y, omq, F, fo);
+  const double S[9] = {0.0, L.om_e, L.om_eps, F.om_d, omq, F.om_d, omq, F.om_s, F.om_s};
+  double Sbar[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double rhob[2] = {0, 0}, jxb[2] = {0, 0}, jyb[2] = {0, 0};
+  double uxb = 0, uyb = 0;
+  const double u2 = F.ux * F.ux + F.uy * F.uy;
+  for (int sp = 0; sp < 2; ++sp) {
+    const double r = F.rho[sp], s = L.s[sp];
+    for (int i = 0; i < 9; ++i) gbar[sp][i] = fbar[sp][i];
+    // f_i = g_i - sum_k M_ki dl_k, dl_k = S_k (m_k - meq_k) / |M_k|^2
+    double mbar[9], meqbar[9];
+    for (int k = 0; k < 9; ++k) {
+      double dlb = 0;
+      for (int i = 0; i < 9; ++i) dlb -= Mki(k, i) * fbar[sp][i];
+      dlb /= Mnorm(k);
+      mbar[k] = S[k] * dlb;
+      meqbar[k] = -S[k] * dlb;
+      Sbar[k] += (F.m[sp][k] - F.meq[sp][k]) * dlb;
+    }
+    for (int i = 0; i < 9; ++i) {
+      double c = 0;
+      for (int k = 0; k < 9; ++k) c += Mki(k, i) * mbar[k];
+      gbar[sp][i] += c;
+    }
+    // meq = rho_s (1, -4 + 2s + 3u^2, 4 - 3s - 3u^2, ux, -ux, uy, -uy, ux^2 - uy^2, ux uy)
+    const double br[9] = {1.0, -4.0 + 2.0 * s + 3.0 * u2, 4.0 - 3.0 * s - 3.0 * u2, F.ux,
+                          -F.ux, F.uy, -F.uy, F.ux * F.ux - F.uy * F.uy, F.ux * F.uy};
+    for (int k = 0; k < 9; ++k) rhob[sp] += meqbar[k] * br[k];
+    uxb += r * (6.0 * F.ux * (meqbar[1] - meqbar[2]) + meqbar[3] - meqbar[4] +
+                2.0 * F.ux * meqbar[7] + F.uy * meqbar[8]);
+    uyb += r * (6.0 * F.uy * (meqbar[1] - meqbar[2]) + meqbar[5] - meqbar[6] -
+                2.0 * F.uy * meqbar[7] + F.ux * meqbar[8]);
+  }
+  const double omdb = Sbar[3] + Sbar[5];
+  *omq_bar = Sbar[4] + Sbar[6];
+  const double omsb = Sbar[7] + Sbar[8];
+  double mxb = 0, nb = 0, lnmub = 0;
+  // om_d = d / (d/2 + c_td); d = m_x br^2; br = sum_s xle_s^{-1/2}
+  const double den = 0.5 * F.d + L.c_td;
+  const double db = omdb * L.c_td / (den * den);
+  mxb += db * F.br * F.br;
+  const double brb = db * 2.0 * F.mx * F.br;
+  for (int sp = 0; sp < 2; ++sp) {
+    const double xleb = brb * (-0.5) / (F.xle[sp] * sqrt(F.xle[sp]));
+    // xle = c_xl Psi_s / n: proportional to mu through c_xl
+    const double Psb = xleb * L.c_xl[sp] / F.n;
+    nb -= xleb * F.xle[sp] / F.n;
+    lnmub += xleb * F.xle[sp];
+    const double lamsb = Psb * F.dPs[sp];
+    // lam_s = c_xl / (s rho_s)
+    rhob[sp] -= lamsb * F.lams[sp] / F.rho[sp];
+    lnmub += lamsb * F.lams[sp];
+  }
+  // om_s = 1 / (1/2 + tsm); tsm = lam Psi(lam) c_ts m_x^{-1/2}
+  const double tsmb = -omsb * F.om_s * F.om_s;
+  const double rsm = L.c_ts / sqrt(F.mx);
+  double lamb = tsmb * (F.Pm + F.lam * F.dPm) * rsm;
+  mxb += tsmb * F.tsm * (-0.5) / F.mx;
+  // lam = c_lam n^{-1} m_x^{-1/2}
+  nb -= lamb * F.lam / F.n;
+  mxb += lamb * F.lam * (-0.5) / F.mx;
+  lnmub += lamb * F.lam;
+  // m_x = rho / n; n = sum s rho_s
+  double rhotb = mxb / F.n;
+  nb -= mxb * F.rho_t / (F.n * F.n);
+  // u = J / rho
+  rhotb -= (uxb * F.ux + uyb * F.uy) / F.rho_t;
+  const double Jxb = uxb / F.rho_t, Jyb = uyb / F.rho_t;
+  for (int sp = 0; sp < 2; ++sp) {
+    rhob[sp] += rhotb + nb * L.s[sp];
+    jxb[sp] += Jxb;
+    jyb[sp] += Jyb;
+    for (int i = 0; i < 9; ++i) gbar[sp][i] += rhob[sp] + CXd[i] * jxb[sp] + CYd[i] * jyb[sp];
+  }
+  *lnmu_bar = lnmub;
+}
+
+// --------------------------------------------------- wall quantities
+// tau_q of Eq. taoq from the pulled wall node (tau'_s(0) in its last term,
+// dx = 1) and the accommodation coefficient (Eq. A12).  With gbar != null
+// also the reverse: given taub = adjoint of tau_q, adds to gbar (the wall
+// node's pulled populations), *alphab and *lnmub.
+__device__ double tau_q(const AL& L, const double g[2][9], double alpha, double taub,
+                        double gbar[2][9], double* alphab, double* lnmub) {
+  const double vs = sqrt(kPiD / 6.0);
+  double rho[2];
+  for (int sp = 0; sp < 2; ++sp) {
+    rho[sp] = 0;
+    for (int i = 0; i < 9; ++i) rho[sp] += g[sp][i];
+  }
+  const double rt = rho[0] + rho[1], n = L.s[0] * rho[0] + L.s[1] * rho[1], mx = rt / n;
+  const double lam = L.c_lam / (n * sqrt(mx));
+  const double gg = L.c_ts / sqrt(mx);
+  const double a = L.H / lam;
+  const Psi3 P = psid(a);
+  const double tt = 0.5 * lam * P.v * gg;
+  const double dtt = 0.5 * gg * (2.0 - P.d1);
+  const double A1 = (2.0 - alpha) / alpha * (1.0 - 0.1817 * alpha);
+  const double A2 = 1.0 / kPiD + 0.5 * A1 * A1;
+  const double Pn = 3.0 + 24.0 * vs * vs * tt * tt * A2;
+  const double Qn = 12.0 + 30.0 * tt * vs * A1;
+  const double tq = 0.5 + Pn / (16.0 * tt) + dtt * Qn / (16.0 * tt * tt);
+  if (!gbar) return tq;
+  const double ttb = taub * (48.0 * vs * vs * tt * A2 / (16.0 * tt) - Pn / (16.0 * tt * tt) +
+                             dtt * 30.0 * vs * A1 / (16.0 * tt * tt) -
+                             2.0 * dtt * Qn / (16.0 * tt * tt * tt));
+  const double dttb = taub * Qn / (16.0 * tt * tt);
+  const double A2b = taub * 24.0 * vs * vs * tt * tt / (16.0 * tt);
+  const double A1b = taub * dtt * 30.0 * vs / (16.0 * tt) + A2b * A1;
+  *alphab += A1b * ((-2.0 / (alpha * alpha)) * (1.0 - 0.1817 * alpha) +
+                    (2.0 - alpha) / alpha * (-0.1817));
+  // tt = lam psi(H/lam) gg / 2, dtt = gg (2 - psi'(H/lam)) / 2
+  double lamb = ttb * 0.5 * gg * (P.v - a * P.d1) + dttb * 0.5 * gg * P.d2 * a / lam;
+  double mxb = (ttb * tt + dttb * dtt) * (-0.5) / mx;
+  double nb = -lamb * lam / n;
+  mxb += lamb * lam * (-0.5) / mx;
+  *lnmub += lamb * lam;
+  const double rtb = mxb / n;
+  nb -= mxb * rt / (n * n);
+  for (int sp = 0; sp < 2; ++sp)
+    for (int i = 0; i < 9; ++i) gbar[sp][i] += rtb + nb * L.s[sp];
+  return tq;
+}
+
+// r of Eq. R (first form) from the reflected post-collision state of the
+// wall node, c_m = c_m0 (2 - alpha)/alpha; dr_drho[2] and dr_dalpha on demand.
+__device__ double dbb_r(const AL& L, const double* f, int x, int j, double alpha,
+                        double* dr_drho, double* dr_dalpha) {
+  double rho[2];
+  for (int sp = 0; sp < 2; ++sp) {
+    rho[sp] = 0;
+    for (int i = 0; i < 9; ++i) rho[sp] += f[fidx(L, sp, i, j, x)];
+  }
+  const double rt = rho[0] + rho[1], n = L.s[0] * rho[0] + L.s[1] * rho[1], mx = rt / n;
+  const double cm = L.c_m0 * (2.0 - alpha) / alpha;
+  const double q = sqrt(kPiD * mx / 6.0);
+  const double den = 1.0 + cm * q;
+  if (dr_drho) {
+    const double drdmx = 2.0 * cm * (kPiD / 6.0) / (2.0 * q) / (den * den);
+    for (int sp = 0; sp < 2; ++sp) dr_drho[sp] = drdmx * (n - rt * L.s[sp]) / (n * n);
+    *dr_dalpha = 2.0 * q / (den * den) * L.c_m0 * (-2.0 / (alpha * alpha));
+  }
+  return 2.0 - 2.0 / den;
+}
+
+// ------------------------------------------------------------ kernels
+// kappa of both ends (Eq. rho2) from the column sums of columns 1, 2 and
+// N_x - 2, N_x - 3 of f; one block.
+__global__ void adj_kappa_kernel(AL L, const double* __restrict__ f, double* __restrict__ kap) {
+  __shared__ double red[4][2][256];  // [end * 2 + species][column 1 or 2 of the end][thread]
+  const int t = threadIdx.x;
+  double acc[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  if (!L.x_periodic) {
+    for (int j = t; j < L.N; j += blockDim.x)
+      for (int sp = 0; sp < 2; ++sp)
+        for (int i = 0; i < 9; ++i) {
+          acc[sp][0] += f[fidx(L, sp, i, j, 1)];
+          acc[sp][1] += f[fidx(L, sp, i, j, 2)];
+          acc[2 + sp][0] += f[fidx(L, sp, i, j, L.Nx - 2)];
+          acc[2 + sp][1] += f[fidx(L, sp, i, j, L.Nx - 3)];
+        }
+  }
+  for (int e = 0; e < 4; ++e) {
+    red[e][0][t] = acc[e][0];
+    red[e][1][t] = acc[e][1];
+  }
+  __syncthreads();
+  if (t == 0) {
+    for (int e = 0; e < 4; ++e) {
+      double c1 = 0, c2 = 0;
+      for (int k = 0; k < (int)blockDim.x; ++k) {
+        c1 += red[e][0][k];
+        c2 += red[e][1][k];
+      }
+      const double target = e < 2 ? L.rho_in[e] : L.rho_out[e - 2];
+      kap[e] = L.x_periodic ? 1.0 : L.N * target / (2.0 * c1 - c2);
+    }
+  }
+}
+
+// r of both walls and 1/tau_q of both halves per column.
+__global__ void adj_cols_kernel(AL L, const double* __restrict__ f, const double* __restrict__ alpha,
+                                StepCols c) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= L.Nx) return;
+  if (!interior(L, x)) {
+    c.r[x] = c.r[L.Nx + x] = 0.0;
+    c.omq[x] = c.omq[L.Nx + x] = 1.0;
+    return;
+  }
+  c.r[x] = dbb_r(L, f, x, 0, alpha[x], nullptr, nullptr);
+  c.r[L.Nx + x] = dbb_r(L, f, x, L.N - 1, alpha[L.Nx + x], nullptr, nullptr);
+}
+__global__ void adj_tauq_kernel(AL L, const double* __restrict__ f, const double* __restrict__ alpha,
+                                StepCols c) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= L.Nx || !interior(L, x)) return;
+  for (int w = 0; w < 2; ++w) {
+    double g[2][9];
+    pull(L, f, c.r, c.kappa, x, w == 0 ? 0 : L.N - 1, g);
+    c.omq[w * L.Nx + x] = 1.0 / tau_q(L, g, alpha[w * L.Nx + x], 0.0, nullptr, nullptr, nullptr);
+  }
+}
+
+// One FP64 step over all nodes: f_out = Collide(Pull(f_in)).
+__global__ void adj_step_kernel(AL L, const double* __restrict__ fin, double* __restrict__ fout,
+                                StepCols c) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (x >= L.Nx || !interior(L, x)) return;
+  double g[2][9], fo[2][9];
+  pull(L, fin, c.r, c.kappa, x, j, g);
+  const int half = (L.N + 1) / 2;
+  const double omq = c.omq[(j < half ? 0 : 1) * L.Nx + x];
+  NodeFwd F;
+  node_forward(L, g, j + 0.5, omq, F, fo);
+  for (int sp = 0; sp < 2; ++sp)
+    for (int i = 0; i < 9; ++i) fout[fidx(L, sp, i, j, x)] = fo[sp][i];
+}
+
+// Initial state (rest equilibrium of the linear pressure and composition
+// profiles) and, with dtheta != null, its derivative with respect to theta.
+__global__ void adj_init_kernel(AL L, double* __restrict__ f, double* __restrict__ dtheta) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (x >= L.Nx) return;
+  const double t = L.x_periodic ? 1.0 : (double)x / (L.Nx - 1);
+  const double n = L.x_periodic ? 1.0 : L.theta + (1.0 - L.theta) * t;
+  const double dn = L.x_periodic ? 0.0 : 1.0 - t;
+  const double Cl = L.C_in + (L.C_out - L.C_in) * t;
+  for (int sp = 0; sp < 2; ++sp) {
+    const double C = sp == L.light ? Cl : 1.0 - Cl;
+    for (int i = 0; i < 9; ++i) {
+      f[fidx(L, sp, i, j, x)] = cwi(L, sp, i) * n * C * L.mh[sp];
+      if (dtheta) dtheta[fidx(L, sp, i, j, x)] = cwi(L, sp, i) * dn * C * L.mh[sp];
+    }
+  }
+}
+
+// Column sums of n_s = s rho_s of a state (for C_l(x)) and of the light
+// species' x momentum.
+__global__ void adj_colsum_kernel(AL L, const double* __restrict__ f, double* __restrict__ out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= L.Nx) return;
+  double nl = 0, nh = 0, jl = 0;
+  for (int j = 0; j < L.N; ++j)
+    for (int i = 0; i < 9; ++i) {
+      const double a = f[fidx(L, L.light, i, j, x)], b = f[fidx(L, 1 - L.light, i, j, x)];
+      nl += L.s[L.light] * a;
+      nh += L.s[1 - L.light] * b;
+      jl += CXd[i] * a;
+    }
+  out[x] = nl;
+  out[L.Nx + x] = nh;
+  out[2 * L.Nx + x] = jl;
+}
+
+// Adjoint of the objective at the final state: CL = (C_in - C_l(x*))/C_in
+// with C_l = S_l / (S_l + S_h) of column x* (objective 0), or the light
+// species' x momentum summed over column N_x - 2 (objective 1).
+__global__ void adj_seed_kernel(AL L, int objective, int xs, double Sl, double Sh,
+                                double* __restrict__ lam) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (x >= L.Nx) return;
+  for (int sp = 0; sp < 2; ++sp)
+    for (int i = 0; i < 9; ++i) {
+      double v = 0.0;
+      if (objective == 0 && x == xs) {
+        const double Sn = Sl + Sh;
+        const double dC = sp == L.light ? Sh / (Sn * Sn) : -Sl / (Sn * Sn);
+        v = -dC * L.s[sp] / L.C_in;
+      } else if (objective == 1 && x == L.Nx - 2 && sp == L.light) {
+        v = CXd[i];
+      }
+      lam[fidx(L, sp, i, j, x)] = v;
+    }
+}
+
+// Reverse of Collide for every node: gbar = (dCollide/dg)^T lam_t; the
+// adjoints of 1/tau_q are summed per column and half, those of ln mu per
+// column (block (32, 8): columns x rows, fixed-order reductions).
+__global__ void adj_rev_node_kernel(AL L, const double* __restrict__ fin,
+                                    const double* __restrict__ lam, StepCols c,
+                                    double* __restrict__ gbar, double* __restrict__ omqbar,
+                                    double* __restrict__ lnmu_col) {
+  __shared__ double red[3][8][32];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x = blockIdx.x * 32 + tx;
+  const int half = (L.N + 1) / 2;
+  double accq[2] = {0, 0}, accm = 0;
+  if (x < L.Nx && interior(L, x)) {
+    for (int j = ty; j < L.N; j += 8) {
+      double g[2][9], fb[2][9], gb[2][9];
+      pull(L, fin, c.r, c.kappa, x, j, g);
+      for (int sp = 0; sp < 2; ++sp)
+        for (int i = 0; i < 9; ++i) fb[sp][i] = lam[fidx(L, sp, i, j, x)];
+      const int h = j < half ? 0 : 1;
+      double oqb, lmb;
+      node_reverse(L, g, j + 0.5, c.omq[h * L.Nx + x], fb, gb, &oqb, &lmb);
+      for (int sp = 0; sp < 2; ++sp)
+        for (int i = 0; i < 9; ++i) gbar[fidx(L, sp, i, j, x)] = gb[sp][i];
+      accq[h] += oqb;
+      accm += lmb;
+    }
+  }
+  red[0][ty][tx] = accq[0];
+  red[1][ty][tx] = accq[1];
+  red[2][ty][tx] = accm;
+  __syncthreads();
+  if (ty == 0 && x < L.Nx) {
+    double a = 0, b = 0, m = 0;
+    for (int k = 0; k < 8; ++k) {
+      a += red[0][k][tx];
+      b += red[1][k][tx];
+      m += red[2][k][tx];
+    }
+    omqbar[x] = a;
+    omqbar[L.Nx + x] = b;
+    lnmu_col[x] += m;
+  }
+}
+
+// Reverse of tau_q per column and wall: adds to the wall nodes' gbar, the
+// accommodation adjoint and ln mu.
+__global__ void adj_rev_tauq_kernel(AL L, const double* __restrict__ fin,
+                                    const double* __restrict__ alpha, StepCols c,
+                                    const double* __restrict__ omqbar, double* __restrict__ gbar,
+                                    double* __restrict__ alphabar, double* __restrict__ lnmu_col) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= L.Nx || !interior(L, x)) return;
+  for (int w = 0; w < 2; ++w) {
+    const int jw = w == 0 ? 0 : L.N - 1;
+    double g[2][9], gb[2][9] = {};
+    pull(L, fin, c.r, c.kappa, x, jw, g);
+    const double omq = c.omq[w * L.Nx + x];
+    const double taub = -omqbar[w * L.Nx + x] * omq * omq;  // omq = 1/tau_q
+    double ab = 0, lmb = 0;
+    tau_q(L, g, alpha[w * L.Nx + x], taub, gb, &ab, &lmb);
+    for (int sp = 0; sp < 2; ++sp)
+      for (int i = 0; i < 9; ++i) gbar[fidx(L, sp, i, jw, x)] += gb[sp][i];
+    alphabar[w * L.Nx + x] += ab;
+    lnmu_col[x] += lmb;
+  }
+}
+
+// Transpose of Pull: lam_prev(x, j) gathers the gbar of every node that
+// pulled population i of node (x, j) - plainly, through the DBB rule of its
+// own wall row, or through a ghost column - and the DBB rule's r adjoint is
+// carried into the wall node's densities and accommodation.  The kappa
+// terms are added by adj_rev_kappa_kernel.
+__global__ void adj_rev_pull_kernel(AL L, const double* __restrict__ fin,
+                                    const double* __restrict__ alpha, StepCols c,
+                                    const double* __restrict__ gbar, double* __restrict__ lamp,
+                                    double* __restrict__ alphabar) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (x >= L.Nx) return;
+  if (!interior(L, x)) {
+    for (int sp = 0; sp < 2; ++sp)
+      for (int i = 0; i < 9; ++i) lamp[fidx(L, sp, i, j, x)] = 0.0;
+    return;
+  }
+  double lp[2][9];
+  for (int sp = 0; sp < 2; ++sp)
+    for (int i = 0; i < 9; ++i) {
+      double v = 0.0;
+      const int xd = wrapx(L, x + CXd[i]), jd = j + CYd[i];
+      if (jd >= 0 && jd < L.N && interior(L, xd)) v += gbar[fidx(L, sp, i, jd, xd)];
+      if (!L.x_periodic) {
+        const bool in_c = (CXd[i] == 1), out_c = (CXd[i] == -1);
+        if (in_c && jd >= 0 && jd < L.N) {
+          if (x == 1) v += 2.0 * c.kappa[sp] * gbar[fidx(L, sp, i, jd, 1)];
+          if (x == 2) v -= c.kappa[sp] * gbar[fidx(L, sp, i, jd, 1)];
+        }
+        if (out_c && jd >= 0 && jd < L.N) {
+          if (x == L.Nx - 2) v += 2.0 * c.kappa[2 + sp] * gbar[fidx(L, sp, i, jd, L.Nx - 2)];
+          if (x == L.Nx - 3) v -= c.kappa[2 + sp] * gbar[fidx(L, sp, i, jd, L.Nx - 2)];
+        }
+      }
+      lp[sp][i] = v;
+    }
+  // diffuse bounce-back: the unknowns (2, 5, 6) at row 0 and (4, 7, 8) at
+  // row N-1 are pulled from this node's own outgoing populations
+  for (int w = 0; w < 2; ++w) {
+    const int jw = w == 0 ? 0 : L.N - 1;
+    if (j != jw) continue;
+    const int unk[3] = {w == 0 ? 2 : 4, w == 0 ? 5 : 7, w == 0 ? 6 : 8};
+    const int out[3] = {w == 0 ? 4 : 2, w == 0 ? 7 : 5, w == 0 ? 8 : 6};
+    const double r = c.r[w * L.Nx + x];
+    double rbar = 0.0;
+    for (int sp = 0; sp < 2; ++sp) {
+      const double G0 = gbar[fidx(L, sp, unk[0], j, x)], G1 = gbar[fidx(L, sp, unk[1], j, x)],
+                   G2 = gbar[fidx(L, sp, unk[2], j, x)];
+      const double o0 = fin[fidx(L, sp, out[0], j, x)], o1 = fin[fidx(L, sp, out[1], j, x)],
+                   o2 = fin[fidx(L, sp, out[2], j, x)];
+      const double S = o0 + o1 + o2;
+      const double T = (2.0 / 3.0) * G0 + (G1 + G2) / 6.0;
+      lp[sp][out[0]] += (1.0 - r) * G0 + r * T;
+      lp[sp][out[1]] += (1.0 - r) * G1 + r * T;
+      lp[sp][out[2]] += (1.0 - r) * G2 + r * T;
+      rbar += G0 * (-o0 + (2.0 / 3.0) * S) + G1 * (-o1 + S / 6.0) + G2 * (-o2 + S / 6.0);
+    }
+    double drr[2], dra;
+    dbb_r(L, fin, x, j, alpha[w * L.Nx + x], drr, &dra);
+    for (int sp = 0; sp < 2; ++sp)
+      for (int i = 0; i < 9; ++i) lp[sp][i] += rbar * drr[sp];
+    alphabar[w * L.Nx + x] += rbar * dra;
+  }
+  for (int sp = 0; sp < 2; ++sp)
+    for (int i = 0; i < 9; ++i) lamp[fidx(L, sp, i, j, x)] = lp[sp][i];
+}
+
+// kappa adjoints (reduced over the end columns' rows), their terms in
+// lam_prev at columns 1, 2 and N_x - 2, N_x - 3, and the theta adjoint of
+// rho_in; one block, fixed order.
+__global__ void adj_rev_kappa_kernel(AL L, const double* __restrict__ fin, StepCols c,
+                                     const double* __restrict__ gbar, double* __restrict__ lamp,
+                                     double* __restrict__ theta_acc) {
+  __shared__ double red[4][256];
+  __shared__ double kb[4], D[4];
+  const int t = threadIdx.x;
+  if (L.x_periodic) return;
+  double acc[4] = {0, 0, 0, 0}, cs[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  for (int jd = t; jd < L.N; jd += blockDim.x)
+    for (int sp = 0; sp < 2; ++sp) {
+      for (int i = 0; i < 9; ++i) {
+        const int js = jd - CYd[i];
+        if (js < 0 || js >= L.N) continue;
+        if (CXd[i] == 1)
+          acc[sp] += gbar[fidx(L, sp, i, jd, 1)] *
+                     (2.0 * fin[fidx(L, sp, i, js, 1)] - fin[fidx(L, sp, i, js, 2)]);
+        if (CXd[i] == -1)
+          acc[2 + sp] += gbar[fidx(L, sp, i, jd, L.Nx - 2)] *
+                         (2.0 * fin[fidx(L, sp, i, js, L.Nx - 2)] -
+                          fin[fidx(L, sp, i, js, L.Nx - 3)]);
+      }
+      for (int i = 0; i < 9; ++i) {
+        cs[sp][0] += fin[fidx(L, sp, i, jd, 1)];
+        cs[sp][1] += fin[fidx(L, sp, i, jd, 2)];
+        cs[2 + sp][0] += fin[fidx(L, sp, i, jd, L.Nx - 2)];
+        cs[2 + sp][1] += fin[fidx(L, sp, i, jd, L.Nx - 3)];
+      }
+    }
+  for (int e = 0; e < 4; ++e) red[e][t] = acc[e];
+  __syncthreads();
+  if (t == 0)
+    for (int e = 0; e < 4; ++e) {
+      double v = 0;
+      for (int k = 0; k < (int)blockDim.x; ++k) v += red[e][k];
+      kb[e] = v;
+    }
+  __syncthreads();
+  for (int e = 0; e < 4; ++e) red[e][t] = 2.0 * cs[e][0] - cs[e][1];
+  __syncthreads();
+  if (t == 0) {
+    for (int e = 0; e < 4; ++e) {
+      double v = 0;
+      for (int k = 0; k < (int)blockDim.x; ++k) v += red[e][k];
+      D[e] = v;
+    }
+    // kappa_in = N rho_in / D, rho_in,s = theta C_s m_s
+    for (int sp = 0; sp < 2; ++sp) *theta_acc += kb[sp] * c.kappa[sp] / L.theta;
+  }
+  __syncthreads();
+  // d kappa / d f(x, j) = -kappa / D * (2 at column 1 (N_x-2), -1 at column 2 (N_x-3))
+  for (int jd = t; jd < L.N; jd += blockDim.x)
+    for (int sp = 0; sp < 2; ++sp) {
+      const double gi = -kb[sp] * c.kappa[sp] / D[sp];
+      const double go = -kb[2 + sp] * c.kappa[2 + sp] / D[2 + sp];
+      for (int i = 0; i < 9; ++i) {
+        lamp[fidx(L, sp, i, jd, 1)] += 2.0 * gi;
+        lamp[fidx(L, sp, i, jd, 2)] -= gi;
+        lamp[fidx(L, sp, i, jd, L.Nx - 2)] += 2.0 * go;
+        lamp[fidx(L, sp, i, jd, L.Nx - 3)] -= go;
+      }
+    }
+}
+
+// sum over the state of a * b into one value per block (fixed order); the
+// host adds the blocks.
+__global__ void adj_dot_kernel(const double* __restrict__ a, const double* __restrict__ b, size_t n,
+                               double* __restrict__ part) {
+  __shared__ double red[256];
+  double v = 0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x)
+    v += a[k] * b[k];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int k = 0; k < (int)blockDim.x; ++k) s += red[k];
+    part[blockIdx.x] = s;
+  }
+}
+
+AL derive_al(const lbm_mix_params* p, int Nx) {
+  AL L;
+  memset(&L, 0, sizeof L);
+  L.N = p->N;
+  L.Nx = Nx;
+  L.x_periodic = p->x_periodic;
+  const double m_min = fmin(p->m_a, p->m_b);
+  L.mh[0] = p->m_a / m_min;
+  L.mh[1] = p->m_b / m_min;
+  L.light = (p->m_a <= p->m_b) ? 0 : 1;
+  L.C_in = p->C_l;
+  L.C_out = p->C_l_out < 0 ? p->C_l : p->C_l_out;
+  L.theta = p->theta;
+  double Ci[2], Co[2];
+  Ci[L.light] = L.C_in;
+  Ci[1 - L.light] = 1.0 - L.C_in;
+  Co[L.light] = L.C_out;
+  Co[1 - L.light] = 1.0 - L.C_out;
+  // mu from lambda_out = Kn_out N at the outlet state (n = 1, p = 1/3)
+  const double mx_out = Co[0] * L.mh[0] + Co[1] * L.mh[1];
+  const double mu = p->Kn_out * p->N * (1.0 / 3.0) / sqrt(kPiD / (6.0 * mx_out));
+  const double mu_s[2] = {p->mu_ratio_a * mu, p->mu_ratio_b * mu};
+  for (int sp = 0; sp < 2; ++sp) {
+    L.s[sp] = 1.0 / L.mh[sp];
+    L.cw[sp][0] = (9.0 - 5.0 * L.s[sp]) / 9.0;
+    L.cw[sp][1] = L.s[sp] / 9.0;
+    L.cw[sp][2] = L.s[sp] / 36.0;
+    L.c_xl[sp] = 3.0 * mu_s[sp] * sqrt(kPiD / (6.0 * L.mh[sp]));
+    L.rho_in[sp] = p->theta * Ci[sp] * L.mh[sp];
+    L.rho_out[sp] = Co[sp] * L.mh[sp];
+  }
+  L.c_lam = 3.0 * mu * sqrt(kPiD / 6.0);
+  L.c_ts = sqrt(6.0 / kPiD);
+  L.c_td = 1.5 * sqrt(3.0 * (L.mh[0] + L.mh[1]) * L.mh[0] * L.mh[1]);
+  L.om_e = 1.0 / p->tau_e;
+  L.om_eps = 1.0 / p->tau_eps;
+  L.c_m0 = p->c_m0;
+  L.H = p->N;
+  return L;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ host side
+struct lbm_adj {
+  AL L;
+  lbm_mix_params p;
+  long T = 0;        // steps of the forward run
+  int K = 0;         // steps between checkpoints
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t S = 0;      // doubles per state
+  double* ckpt = nullptr;   // [ceil(T/K)+1][S] states at steps 0, K, 2K, ...
+  double* seg = nullptr;    // [K][S] replayed inputs of one segment's steps
+  double* segcols = nullptr;  // [K][4 Nx + 4] column data of those steps
+  double* work[2] = {nullptr, nullptr};
+  double* lam[2] = {nullptr, nullptr};
+  double* gbar = nullptr;
+  double* dtheta0 = nullptr;  // d f^0 / d theta
+  double* alpha = nullptr;    // [2][Nx]
+  double* alphabar = nullptr;
+  double* omqbar = nullptr;   // [2][Nx]
+  double* lnmu_col = nullptr; // [Nx]
+  double* theta_acc = nullptr;  // [1]
+  double* colsum = nullptr;   // [3][Nx]
+  double* part = nullptr;     // [256]
+  double* h_col = nullptr;    // host copy of colsum
+  bool have_forward = false;
+  double CL = 0, flux = 0, Sl = 0, Sh = 0;
+  int xstar = -1;
+};
+
+namespace {
+
+StepCols cols_of(lbm_adj* a, double* base) {
+  StepCols c;
+  c.r = base;
+  c.omq = base + 2 * a->L.Nx;
+  c.kappa = base + 4 * a->L.Nx;
+  return c;
+}
+
+// Forward step from f (input) into fo, column data into cols.
+int fwd_step(lbm_adj* a, const double* f, double* fo, StepCols c) {
+  const AL& L = a->L;
+  adj_kappa_kernel<<<1, 256, 0, a->stream>>>(L, f, c.kappa);
+  const int cb = (L.Nx + 127) / 128;
+  adj_cols_kernel<<<cb, 128, 0, a->stream>>>(L, f, a->alpha, c);
+  adj_tauq_kernel<<<cb, 128, 0, a->stream>>>(L, f, a->alpha, c);
+  dim3 grd(cb, L.N);
+  adj_step_kernel<<<grd, 128, 0, a->stream>>>(L, f, fo, c);
+  CKA(cudaGetLastError());
+  return LBM_OK;
+}
+
+int objective_from_state(lbm_adj* a, const double* f) {
+  const AL& L = a->L;
+  adj_colsum_kernel<<<(L.Nx + 127) / 128, 128, 0, a->stream>>>(L, f, a->colsum);
+  CKA(cudaGetLastError());
+  CKA(cudaMemcpyAsync(a->h_col, a->colsum, sizeof(double) * 3 * L.Nx, cudaMemcpyDeviceToHost,
+                      a->stream));
+  CKA(cudaStreamSynchronize(a->stream));
+  // C_l(x) over the updated columns; ties go to the smaller x
+  double cmin = INFINITY;
+  int xs = -1;
+  const int x0 = L.x_periodic ? 0 : 1, x1 = L.x_periodic ? L.Nx - 1 : L.Nx - 2;
+  for (int x = x0; x <= x1; ++x) {
+    const double C = a->h_col[x] / (a->h_col[x] + a->h_col[L.Nx + x]);
+    if (C < cmin) {
+      cmin = C;
+      xs = x;
+    }
+  }
+  a->xstar = xs;
+  a->Sl = a->h_col[xs];
+  a->Sh = a->h_col[L.Nx + xs];
+  a->CL = (L.C_in - cmin) / L.C_in;
+  a->flux = a->h_col[2 * L.Nx + (L.Nx - 2)];
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_adj_create(const lbm_mix_params* p, long nsteps, int checkpoint_every, void* stream,
+                   lbm_adj** out) {
+  if (!out) return lbm_internal_error(LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  int Nx = 0;
+  int st = lbm_internal_validate(p, &Nx);
+  if (st) return st;
+  if (nsteps < 1 || checkpoint_every < 1)
+    return lbm_internal_error(LBM_EINVAL, "need nsteps >= 1 and checkpoint_every >= 1");
+  if (!p->x_periodic && Nx < 4) return lbm_internal_error(LBM_EINVAL, "need N_x >= 4");
+  lbm_adj* a = new (std::nothrow) lbm_adj;
+  if (!a) return lbm_internal_error(LBM_ENOMEM, "host allocation failed");
+  a->p = *p;
+  a->L = derive_al(p, Nx);
+  a->T = nsteps;
+  a->K = checkpoint_every < nsteps ? checkpoint_every : (int)nsteps;
+  a->S = (size_t)18 * p->N * Nx;
+  if (stream) {
+    a->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&a->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete a;
+      return lbm_internal_error(LBM_ECUDA, "cudaStreamCreate failed");
+    }
+    a->own_stream = true;
+  }
+  const long nck = (nsteps + a->K - 1) / a->K + 1;
+  const size_t cw = 4 * (size_t)Nx + 4;
+  cudaError_t e = cudaSuccess;
+#define ALLOCA(ptr, bytes) \
+  if (e == cudaSuccess) e = cudaMalloc((void**)&(ptr), (bytes))
+  ALLOCA(a->ckpt, sizeof(double) * a->S * nck);
+  ALLOCA(a->seg, sizeof(double) * a->S * a->K);
+  ALLOCA(a->segcols, sizeof(double) * cw * a->K);
+  ALLOCA(a->work[0], sizeof(double) * a->S);
+  ALLOCA(a->work[1], sizeof(double) * a->S);
+  ALLOCA(a->lam[0], sizeof(double) * a->S);
+  ALLOCA(a->lam[1], sizeof(double) * a->S);
+  ALLOCA(a->gbar, sizeof(double) * a->S);
+  ALLOCA(a->dtheta0, sizeof(double) * a->S);
+  ALLOCA(a->alpha, sizeof(double) * 2 * Nx);
+  ALLOCA(a->alphabar, sizeof(double) * 2 * Nx);
+  ALLOCA(a->omqbar, sizeof(double) * 2 * Nx);
+  ALLOCA(a->lnmu_col, sizeof(double) * Nx);
+  ALLOCA(a->theta_acc, sizeof(double));
+  ALLOCA(a->colsum, sizeof(double) * 3 * Nx);
+  ALLOCA(a->part, sizeof(double) * 256);
+#undef ALLOCA
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&a->h_col, sizeof(double) * (3 * Nx + 256));
+  if (e == cudaSuccess) {
+    double* al = (double*)malloc(sizeof(double) * 2 * Nx);
+    if (!al) {
+      e = cudaErrorMemoryAllocation;
+    } else {
+      for (int k = 0; k < 2 * Nx; ++k) al[k] = p->accommodation;
+      e = cudaMemcpyAsync(a->alpha, al, sizeof(double) * 2 * Nx, cudaMemcpyHostToDevice, a->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(a->stream);
+      free(al);
+    }
+  }
+  if (e != cudaSuccess) {
+    const int code = e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+    lbm_internal_error(code, "adjoint allocation failed: %s", cudaGetErrorString(e));
+    cudaGetLastError();
+    lbm_adj_destroy(a);
+    return code;
+  }
+  *out = a;
+  return LBM_OK;
+}
+
+void lbm_adj_destroy(lbm_adj* a) {
+  if (!a) return;
+  if (a->stream) cudaStreamSynchronize(a->stream);
+  cudaFree(a->ckpt);
+  cudaFree(a->seg);
+  cudaFree(a->segcols);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(a->work[k]);
+    cudaFree(a->lam[k]);
+  }
+  cudaFree(a->gbar);
+  cudaFree(a->dtheta0);
+  cudaFree(a->alpha);
+  cudaFree(a->alphabar);
+  cudaFree(a->omqbar);
+  cudaFree(a->lnmu_col);
+  cudaFree(a->theta_acc);
+  cudaFree(a->colsum);
+  cudaFree(a->part);
+  cudaFreeHost(a->h_col);
+  if (a->own_stream && a->stream) cudaStreamDestroy(a->stream);
+  delete a;
+}
+
+int lbm_adj_set_accommodation_field(lbm_adj* a, const double* alpha, long n) {
+  if (!a || !alpha) return lbm_internal_error(LBM_EINVAL, "NULL argument");
+  if (n != 2L * a->L.Nx) return lbm_internal_error(LBM_EINVAL, "need 2 N_x = %d values", 2 * a->L.Nx);
+  for (long k = 0; k < n; ++k)
+    if (!(alpha[k] > 0 && alpha[k] <= 1))
+      return lbm_internal_error(LBM_EINVAL, "accommodation[%ld] = %g not in (0, 1]", k, alpha[k]);
+  CKA(cudaMemcpyAsync(a->alpha, alpha, sizeof(double) * n, cudaMemcpyHostToDevice, a->stream));
+  CKA(cudaStreamSynchronize(a->stream));
+  a->have_forward = false;
+  return LBM_OK;
+}
+
+int lbm_adj_forward(lbm_adj* a, double* CL, double* flux) {
+  if (!a) return lbm_internal_error(LBM_EINVAL, "handle is NULL");
+  const AL& L = a->L;
+  const dim3 grd((L.Nx + 127) / 128, L.N);
+  adj_init_kernel<<<grd, 128, 0, a->stream>>>(L, a->ckpt, a->dtheta0);
+  CKA(cudaGetLastError());
+  const double* f = a->ckpt;
+  for (long t = 1; t <= a->T; ++t) {
+    double* fo = (t % a->K == 0) ? a->ckpt + a->S * (size_t)(t / a->K) : a->work[t & 1];
+    int st = fwd_step(a, f, fo, cols_of(a, a->segcols));
+    if (st) return st;
+    f = fo;
+  }
+  int st = objective_from_state(a, f);
+  if (st) return st;
+  if (!isfinite(a->CL)) return lbm_internal_error(LBM_ENONFINITE, "non-finite forward state");
+  a->have_forward = true;
+  if (CL) *CL = a->CL;
+  if (flux) *flux = a->flux;
+  return LBM_OK;
+}
+
+int lbm_adj_state(lbm_adj* a, double* f, long n) {
+  if (!a || !f) return lbm_internal_error(LBM_EINVAL, "NULL argument");
+  if (!a->have_forward) return lbm_internal_error(LBM_EINVAL, "run lbm_adj_forward first");
+  if (n != (long)a->S) return lbm_internal_error(LBM_EINVAL, "need %zu values", a->S);
+  const double* last = (a->T % a->K == 0) ? a->ckpt + a->S * (size_t)(a->T / a->K)
+                                           : a->work[a->T & 1];
+  CKA(cudaMemcpyAsync(f, last, sizeof(double) * a->S, cudaMemcpyDeviceToHost, a->stream));
+  CKA(cudaStreamSynchronize(a->stream));
+  return LBM_OK;
+}
+
+int lbm_adj_gradient(lbm_adj* a, int objective, double* dtheta, double* dkn, double* dalpha,
+                     long n_alpha) {
+  if (!a) return lbm_internal_error(LBM_EINVAL, "handle is NULL");
+  if (objective != LBM_ADJ_CL && objective != LBM_ADJ_FLUX)
+    return lbm_internal_error(LBM_EINVAL, "unknown objective %d", objective);
+  if (!a->have_forward) return lbm_internal_error(LBM_EINVAL, "run lbm_adj_forward first");
+  const AL& L = a->L;
+  if (dalpha && n_alpha != 2L * L.Nx)
+    return lbm_internal_error(LBM_EINVAL, "dalpha needs 2 N_x = %d values", 2 * L.Nx);
+  const dim3 grd((L.Nx + 127) / 128, L.N);
+  const int cb = (L.Nx + 127) / 128;
+  const size_t cw = 4 * (size_t)L.Nx + 4;
+  CKA(cudaMemsetAsync(a->alphabar, 0, sizeof(double) * 2 * L.Nx, a->stream));
+  CKA(cudaMemsetAsync(a->lnmu_col, 0, sizeof(double) * L.Nx, a->stream));
+  CKA(cudaMemsetAsync(a->theta_acc, 0, sizeof(double), a->stream));
+  adj_seed_kernel<<<grd, 128, 0, a->stream>>>(L, objective, a->xstar, a->Sl, a->Sh, a->lam[0]);
+  CKA(cudaGetLastError());
+  int cur = 0;  // lam[cur] is the adjoint of the state after the step being reversed
+  const long nseg = (a->T + a->K - 1) / a->K;
+  for (long sg = nseg - 1; sg >= 0; --sg) {
+    const long t0 = sg * a->K;  // segment replays steps t0+1 .. t1
+    const long t1 = (t0 + a->K < a->T) ? t0 + a->K : a->T;
+    // replay: inputs f^{t0} .. f^{t1-1} into seg, column data into segcols
+    CKA(cudaMemcpyAsync(a->seg, a->ckpt + a->S * (size_t)sg, sizeof(double) * a->S,
+                        cudaMemcpyDeviceToDevice, a->stream));
+    for (long t = t0 + 1; t <= t1; ++t) {
+      const long k = t - t0 - 1;
+      double* fin = a->seg + a->S * (size_t)k;
+      double* fo = (t < t1) ? a->seg + a->S * (size_t)(k + 1) : a->work[0];
+      int st = fwd_step(a, fin, fo, cols_of(a, a->segcols + cw * k));
+      if (st) return st;
+    }
+    for (long t = t1; t > t0; --t) {
+      const long k = t - t0 - 1;
+      const double* fin = a->seg + a->S * (size_t)k;
+      StepCols c = cols_of(a, a->segcols + cw * k);
+      adj_rev_node_kernel<<<(L.Nx + 31) / 32, dim3(32, 8), 0, a->stream>>>(
+          L, fin, a->lam[cur], c, a->gbar, a->omqbar, a->lnmu_col);
+      adj_rev_tauq_kernel<<<cb, 128, 0, a->stream>>>(L, fin, a->alpha, c, a->omqbar, a->gbar,
+                                                     a->alphabar, a->lnmu_col);
+      adj_rev_pull_kernel<<<grd, 128, 0, a->stream>>>(L, fin, a->alpha, c, a->gbar,
+                                                      a->lam[1 - cur], a->alphabar);
+      adj_rev_kappa_kernel<<<1, 256, 0, a->stream>>>(L, fin, c, a->gbar, a->lam[1 - cur],
+                                                      a->theta_acc);
+      CKA(cudaGetLastError());
+      cur = 1 - cur;
+    }
+  }
+  // theta through the initial state: lam^0 . d f^0 / d theta
+  adj_dot_kernel<<<256, 256, 0, a->stream>>>(a->lam[cur], a->dtheta0, a->S, a->part);
+  CKA(cudaGetLastError());
+  double* h = a->h_col;  // staging: [Nx] ln mu, [1] theta, [256] parts
+  CKA(cudaMemcpyAsync(h, a->lnmu_col, sizeof(double) * L.Nx, cudaMemcpyDeviceToHost, a->stream));
+  CKA(cudaMemcpyAsync(h + L.Nx, a->theta_acc, sizeof(double), cudaMemcpyDeviceToHost, a->stream));
+  CKA(cudaMemcpyAsync(h + L.Nx + 1, a->part, sizeof(double) * 256, cudaMemcpyDeviceToHost,
+                      a->stream));
+  if (dalpha)
+    CKA(cudaMemcpyAsync(dalpha, a->alphabar, sizeof(double) * 2 * L.Nx, cudaMemcpyDeviceToHost,
+                        a->stream));
+  CKA(cudaStreamSynchronize(a->stream));
+  double lnmu = 0, th = h[L.Nx];
+  for (int x = 0; x < L.Nx; ++x) lnmu += h[x];
+  for (int k = 0; k < 256; ++k) th += h[L.Nx + 1 + k];
+  if (dtheta) *dtheta = th;
+  if (dkn) *dkn = lnmu / a->p.Kn_out;  // mu is proportional to Kn_out
+  return LBM_OK;
+}
+
+}  // extern "C"

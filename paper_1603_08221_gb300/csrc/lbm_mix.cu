@@ -38,6 +38,7 @@
 #include <new>
 
 #include "../../include/lbm_mix.h"
+#include "lbm_internal.h"
 
 namespace {
 
@@ -2270,3 +2271,14 @@ int lbm_sweep_schedule(lbm_sweep* s, int* policy, int* rows_per_block, double* r
 }
 
 }  // extern "C"
+
+// ------------------------------------------- helpers for other translation units
+int lbm_internal_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int lbm_internal_validate(const lbm_mix_params* p, int* Nx_out) { return validate(p, Nx_out); }
