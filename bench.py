@@ -201,6 +201,45 @@ def run_sweep(args, rank, world, barrier):
             "autotuned_policy": policy, "autotune_block_ms": round_ms}
 
 
+def run_adjoint(args, stream):
+    """The sensitivity workload (He-Ar 1280 x 64, 5000 steps, checkpoints
+    every 70 steps, accommodation 1 - U(0, 0.05) per wall node): FP64
+    forward, one backward sweep for dCL/d(theta, Kn_out, alpha), and the FP32
+    forward of the same steps for the adjoint/forward time ratio."""
+    import numpy as np
+    import torch
+    from paper_1603_08221_gb300 import binding, workloads
+    p = workloads.preset("heli_argon_1280x64")
+    nx = workloads.n_x(p)
+    alpha = workloads.random_accommodation(nx, 1).reshape(2, nx)
+    steps, ck = 5000, 70
+    a = binding.LbmAdjoint(p, steps, ck, alpha, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cl, _ = a.forward()
+    t_fwd64 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g = a.gradient(binding.LBM_ADJ_CL)
+    t_grad = time.perf_counter() - t0
+    a.close()
+    f = binding.LbmMix(stream=stream, **p)
+    f.init()
+    f.set_accommodation_field(np.ascontiguousarray(alpha.ravel()))
+    f.step(10)
+    f.sync()
+    t0 = time.perf_counter()
+    f.step(steps)
+    f.sync()
+    t_fwd32 = time.perf_counter() - t0
+    return {"workload": "heli_argon_1280x64", "steps": steps, "checkpoint_every": ck,
+            "objective": "CL", "CL": cl, "dCL_dtheta": g["theta"], "dCL_dKn_out": g["Kn_out"],
+            "dCL_dalpha_norm": float(np.linalg.norm(g["alpha"])),
+            "forward_fp64_s": t_fwd64, "gradient_s": t_grad, "forward_fp32_s": t_fwd32,
+            "adjoint_over_fp64_forward": t_grad / t_fwd64,
+            "adjoint_over_fp32_forward": t_grad / t_fwd32,
+            "dtype": "f64 (forward replay and adjoint)"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -318,6 +357,7 @@ def run_ours(args):
             del v
 
     sweep = None if args.no_sweep else run_sweep(args, rank, world, barrier)
+    adjoint = None if (args.no_adjoint or rank != 0) else run_adjoint(args, stream)
 
     # ---------------- whole-job aggregation (max time over ranks)
     if world > 1:
@@ -361,6 +401,7 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "storage_variants": variants or None,
         "sweep": sweep,
+        "adjoint": adjoint,
         "clocks": clk.summary(),
         "result": {"CL": sep["CL"], "Cl_tilde": sep["Cl_tilde"], "mdot_a": sep["mdot_a"],
                    "mdot_b": sep["mdot_b"], "CL_e2e_run": sep_e2e["CL"]},
@@ -385,6 +426,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the BF16/FP16 storage timings")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint (gradient) timing")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the 96-channel parametric sweep")
     ap.add_argument("--sweep-cap", type=int, default=10000,

@@ -162,6 +162,7 @@ __device__ double src(const AL& L, const double* f, const double* kap, int sp, i
 __device__ void pull(const AL& L, const double* f, const double* r2, const double* kap, int x,
                      int j, double g[2][9]) {
   const double rb = r2[x], rt = r2[L.Nx + x];
+  #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     double* q = g[sp];
     q[0] = f[fidx(L, sp, 0, j, x)];
@@ -236,8 +237,10 @@ __device__ double half_psi(double y, double H, double lam, double* dlam) {
 // f' = g - M^{-1} S (m - m^eq).
 __device__ void node_forward(const AL& L, const double g[2][9], double y, double omq,
                              NodeFwd& F, double fo[2][9]) {
+  #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     double r = 0, jx = 0, jy = 0;
+    #pragma unroll
     for (int i = 0; i < 9; ++i) {
       r += g[sp][i];
       jx += CXd[i] * g[sp][i];
@@ -257,6 +260,7 @@ __device__ void node_forward(const AL& L, const double g[2][9], double y, double
   F.tsm = F.lam * F.Pm * L.c_ts / sqrt(F.mx);
   F.om_s = 1.0 / (0.5 + F.tsm);
   F.br = 0.0;
+  #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     F.lams[sp] = L.c_xl[sp] / (L.s[sp] * F.rho[sp]);
     F.Ps[sp] = half_psi(y, L.H, F.lams[sp], &F.dPs[sp]);
@@ -267,20 +271,25 @@ __device__ void node_forward(const AL& L, const double g[2][9], double y, double
   F.om_d = F.d / (0.5 * F.d + L.c_td);
   const double u2 = F.ux * F.ux + F.uy * F.uy;
   const double S[9] = {0.0, L.om_e, L.om_eps, F.om_d, omq, F.om_d, omq, F.om_s, F.om_s};
+  #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     const double r = F.rho[sp], s = L.s[sp];
     const double br[9] = {1.0, -4.0 + 2.0 * s + 3.0 * u2, 4.0 - 3.0 * s - 3.0 * u2, F.ux,
                           -F.ux, F.uy, -F.uy, F.ux * F.ux - F.uy * F.uy, F.ux * F.uy};
     double dl[9];
+    #pragma unroll
     for (int k = 0; k < 9; ++k) {
       double mk = 0;
+      #pragma unroll
       for (int i = 0; i < 9; ++i) mk += Mki(k, i) * g[sp][i];
       F.m[sp][k] = mk;
       F.meq[sp][k] = r * br[k];
       dl[k] = S[k] * (mk - F.meq[sp][k]) / Mnorm(k);
     }
+    #pragma unroll
     for (int i = 0; i < 9; ++i) {
       double c = 0;
+      #pragma unroll
       for (int k = 0; k < 9; ++k) c += Mki(k, i) * dl[k];
       fo[sp][i] = g[sp][i] - c;
     }
@@ -301,27 +310,34 @@ __device__ void node_reverse(const AL& L, const double g[2][9], double y, double
   double rhob[2] = {0, 0}, jxb[2] = {0, 0}, jyb[2] = {0, 0};
   double uxb = 0, uyb = 0;
   const double u2 = F.ux * F.ux + F.uy * F.uy;
+  #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     const double r = F.rho[sp], s = L.s[sp];
+    #pragma unroll
     for (int i = 0; i < 9; ++i) gbar[sp][i] = fbar[sp][i];
     // f_i = g_i - sum_k M_ki dl_k, dl_k = S_k (m_k - meq_k) / |M_k|^2
     double mbar[9], meqbar[9];
+    #pragma unroll
     for (int k = 0; k < 9; ++k) {
       double dlb = 0;
+      #pragma unroll
       for (int i = 0; i < 9; ++i) dlb -= Mki(k, i) * fbar[sp][i];
       dlb /= Mnorm(k);
       mbar[k] = S[k] * dlb;
       meqbar[k] = -S[k] * dlb;
       Sbar[k] += (F.m[sp][k] - F.meq[sp][k]) * dlb;
     }
+    #pragma unroll
     for (int i = 0; i < 9; ++i) {
       double c = 0;
+      #pragma unroll
       for (int k = 0; k < 9; ++k) c += Mki(k, i) * mbar[k];
       gbar[sp][i] += c;
     }
     // meq = rho_s (1, -4 + 2s + 3u^2, 4 - 3s - 3u^2, ux, -ux, uy, -uy, ux^2 - uy^2, ux uy)
     const double br[9] = {1.0, -4.0 + 2.0 * s + 3.0 * u2, 4.0 - 3.0 * s - 3.0 * u2, F.ux,
                           -F.ux, F.uy, -F.uy, F.ux * F.ux - F.uy * F.uy, F.ux * F.uy};
+    #pragma unroll
     for (int k = 0; k < 9; ++k) rhob[sp] += meqbar[k] * br[k];
     uxb += r * (6.0 * F.ux * (meqbar[1] - meqbar[2]) + meqbar[3] - meqbar[4] +
                 2.0 * F.ux * meqbar[7] + F.uy * meqbar[8]);
@@ -337,6 +353,7 @@ __device__ void node_reverse(const AL& L, const double g[2][9], double y, double
   const double db = omdb * L.c_td / (den * den);
   mxb += db * F.br * F.br;
   const double brb = db * 2.0 * F.mx * F.br;
+  #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     const double xleb = brb * (-0.5) / (F.xle[sp] * sqrt(F.xle[sp]));
     // xle = c_xl Psi_s / n: proportional to mu through c_xl
@@ -363,10 +380,12 @@ __device__ void node_reverse(const AL& L, const double g[2][9], double y, double
   // u = J / rho
   rhotb -= (uxb * F.ux + uyb * F.uy) / F.rho_t;
   const double Jxb = uxb / F.rho_t, Jyb = uyb / F.rho_t;
+  #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     rhob[sp] += rhotb + nb * L.s[sp];
     jxb[sp] += Jxb;
     jyb[sp] += Jyb;
+    #pragma unroll
     for (int i = 0; i < 9; ++i) gbar[sp][i] += rhob[sp] + CXd[i] * jxb[sp] + CYd[i] * jyb[sp];
   }
   *lnmu_bar = lnmub;
@@ -381,8 +400,10 @@ __device__ double tau_q(const AL& L, const double g[2][9], double alpha, double 
                         double gbar[2][9], double* alphab, double* lnmub) {
   const double vs = sqrt(kPiD / 6.0);
   double rho[2];
+  #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     rho[sp] = 0;
+    #pragma unroll
     for (int i = 0; i < 9; ++i) rho[sp] += g[sp][i];
   }
   const double rt = rho[0] + rho[1], n = L.s[0] * rho[0] + L.s[1] * rho[1], mx = rt / n;
@@ -414,7 +435,9 @@ __device__ double tau_q(const AL& L, const double g[2][9], double alpha, double 
   *lnmub += lamb * lam;
   const double rtb = mxb / n;
   nb -= mxb * rt / (n * n);
+  #pragma unroll
   for (int sp = 0; sp < 2; ++sp)
+    #pragma unroll
     for (int i = 0; i < 9; ++i) gbar[sp][i] += rtb + nb * L.s[sp];
   return tq;
 }
@@ -424,8 +447,10 @@ __device__ double tau_q(const AL& L, const double g[2][9], double alpha, double 
 __device__ double dbb_r(const AL& L, const double* f, int x, int j, double alpha,
                         double* dr_drho, double* dr_dalpha) {
   double rho[2];
+  #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     rho[sp] = 0;
+    #pragma unroll
     for (int i = 0; i < 9; ++i) rho[sp] += f[fidx(L, sp, i, j, x)];
   }
   const double rt = rho[0] + rho[1], n = L.s[0] * rho[0] + L.s[1] * rho[1], mx = rt / n;
@@ -434,6 +459,7 @@ __device__ double dbb_r(const AL& L, const double* f, int x, int j, double alpha
   const double den = 1.0 + cm * q;
   if (dr_drho) {
     const double drdmx = 2.0 * cm * (kPiD / 6.0) / (2.0 * q) / (den * den);
+    #pragma unroll
     for (int sp = 0; sp < 2; ++sp) dr_drho[sp] = drdmx * (n - rt * L.s[sp]) / (n * n);
     *dr_dalpha = 2.0 * q / (den * den) * L.c_m0 * (-2.0 / (alpha * alpha));
   }
@@ -449,7 +475,9 @@ __global__ void adj_kappa_kernel(AL L, const double* __restrict__ f, double* __r
   double acc[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
   if (!L.x_periodic) {
     for (int j = t; j < L.N; j += blockDim.x)
+      #pragma unroll
       for (int sp = 0; sp < 2; ++sp)
+        #pragma unroll
         for (int i = 0; i < 9; ++i) {
           acc[sp][0] += f[fidx(L, sp, i, j, 1)];
           acc[sp][1] += f[fidx(L, sp, i, j, 2)];
@@ -511,7 +539,9 @@ __global__ void adj_step_kernel(AL L, const double* __restrict__ fin, double* __
   const double omq = c.omq[(j < half ? 0 : 1) * L.Nx + x];
   NodeFwd F;
   node_forward(L, g, j + 0.5, omq, F, fo);
+  #pragma unroll
   for (int sp = 0; sp < 2; ++sp)
+    #pragma unroll
     for (int i = 0; i < 9; ++i) fout[fidx(L, sp, i, j, x)] = fo[sp][i];
 }
 
@@ -525,8 +555,10 @@ __global__ void adj_init_kernel(AL L, double* __restrict__ f, double* __restrict
   const double n = L.x_periodic ? 1.0 : L.theta + (1.0 - L.theta) * t;
   const double dn = L.x_periodic ? 0.0 : 1.0 - t;
   const double Cl = L.C_in + (L.C_out - L.C_in) * t;
+  #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     const double C = sp == L.light ? Cl : 1.0 - Cl;
+    #pragma unroll
     for (int i = 0; i < 9; ++i) {
       f[fidx(L, sp, i, j, x)] = cwi(L, sp, i) * n * C * L.mh[sp];
       if (dtheta) dtheta[fidx(L, sp, i, j, x)] = cwi(L, sp, i) * dn * C * L.mh[sp];
@@ -541,6 +573,7 @@ __global__ void adj_colsum_kernel(AL L, const double* __restrict__ f, double* __
   if (x >= L.Nx) return;
   double nl = 0, nh = 0, jl = 0;
   for (int j = 0; j < L.N; ++j)
+    #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const double a = f[fidx(L, L.light, i, j, x)], b = f[fidx(L, 1 - L.light, i, j, x)];
       nl += L.s[L.light] * a;
@@ -560,7 +593,9 @@ __global__ void adj_seed_kernel(AL L, int objective, int xs, double Sl, double S
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (x >= L.Nx) return;
+  #pragma unroll
   for (int sp = 0; sp < 2; ++sp)
+    #pragma unroll
     for (int i = 0; i < 9; ++i) {
       double v = 0.0;
       if (objective == 0 && x == xs) {
@@ -590,12 +625,16 @@ __global__ void adj_rev_node_kernel(AL L, const double* __restrict__ fin,
     for (int j = ty; j < L.N; j += 8) {
       double g[2][9], fb[2][9], gb[2][9];
       pull(L, fin, c.r, c.kappa, x, j, g);
+      #pragma unroll
       for (int sp = 0; sp < 2; ++sp)
+        #pragma unroll
         for (int i = 0; i < 9; ++i) fb[sp][i] = lam[fidx(L, sp, i, j, x)];
       const int h = j < half ? 0 : 1;
       double oqb, lmb;
       node_reverse(L, g, j + 0.5, c.omq[h * L.Nx + x], fb, gb, &oqb, &lmb);
+      #pragma unroll
       for (int sp = 0; sp < 2; ++sp)
+        #pragma unroll
         for (int i = 0; i < 9; ++i) gbar[fidx(L, sp, i, j, x)] = gb[sp][i];
       accq[h] += oqb;
       accm += lmb;
@@ -634,7 +673,9 @@ __global__ void adj_rev_tauq_kernel(AL L, const double* __restrict__ fin,
     const double taub = -omqbar[w * L.Nx + x] * omq * omq;  // omq = 1/tau_q
     double ab = 0, lmb = 0;
     tau_q(L, g, alpha[w * L.Nx + x], taub, gb, &ab, &lmb);
+    #pragma unroll
     for (int sp = 0; sp < 2; ++sp)
+      #pragma unroll
       for (int i = 0; i < 9; ++i) gbar[fidx(L, sp, i, jw, x)] += gb[sp][i];
     alphabar[w * L.Nx + x] += ab;
     lnmu_col[x] += lmb;
@@ -654,12 +695,16 @@ __global__ void adj_rev_pull_kernel(AL L, const double* __restrict__ fin,
   const int j = blockIdx.y;
   if (x >= L.Nx) return;
   if (!interior(L, x)) {
+    #pragma unroll
     for (int sp = 0; sp < 2; ++sp)
+      #pragma unroll
       for (int i = 0; i < 9; ++i) lamp[fidx(L, sp, i, j, x)] = 0.0;
     return;
   }
   double lp[2][9];
+  #pragma unroll
   for (int sp = 0; sp < 2; ++sp)
+    #pragma unroll
     for (int i = 0; i < 9; ++i) {
       double v = 0.0;
       const int xd = wrapx(L, x + CXd[i]), jd = j + CYd[i];
@@ -686,6 +731,7 @@ __global__ void adj_rev_pull_kernel(AL L, const double* __restrict__ fin,
     const int out[3] = {w == 0 ? 4 : 2, w == 0 ? 7 : 5, w == 0 ? 8 : 6};
     const double r = c.r[w * L.Nx + x];
     double rbar = 0.0;
+    #pragma unroll
     for (int sp = 0; sp < 2; ++sp) {
       const double G0 = gbar[fidx(L, sp, unk[0], j, x)], G1 = gbar[fidx(L, sp, unk[1], j, x)],
                    G2 = gbar[fidx(L, sp, unk[2], j, x)];
@@ -700,11 +746,15 @@ __global__ void adj_rev_pull_kernel(AL L, const double* __restrict__ fin,
     }
     double drr[2], dra;
     dbb_r(L, fin, x, j, alpha[w * L.Nx + x], drr, &dra);
+    #pragma unroll
     for (int sp = 0; sp < 2; ++sp)
+      #pragma unroll
       for (int i = 0; i < 9; ++i) lp[sp][i] += rbar * drr[sp];
     alphabar[w * L.Nx + x] += rbar * dra;
   }
+  #pragma unroll
   for (int sp = 0; sp < 2; ++sp)
+    #pragma unroll
     for (int i = 0; i < 9; ++i) lamp[fidx(L, sp, i, j, x)] = lp[sp][i];
 }
 
@@ -720,7 +770,9 @@ __global__ void adj_rev_kappa_kernel(AL L, const double* __restrict__ fin, StepC
   if (L.x_periodic) return;
   double acc[4] = {0, 0, 0, 0}, cs[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
   for (int jd = t; jd < L.N; jd += blockDim.x)
+    #pragma unroll
     for (int sp = 0; sp < 2; ++sp) {
+      #pragma unroll
       for (int i = 0; i < 9; ++i) {
         const int js = jd - CYd[i];
         if (js < 0 || js >= L.N) continue;
@@ -732,6 +784,7 @@ __global__ void adj_rev_kappa_kernel(AL L, const double* __restrict__ fin, StepC
                          (2.0 * fin[fidx(L, sp, i, js, L.Nx - 2)] -
                           fin[fidx(L, sp, i, js, L.Nx - 3)]);
       }
+      #pragma unroll
       for (int i = 0; i < 9; ++i) {
         cs[sp][0] += fin[fidx(L, sp, i, jd, 1)];
         cs[sp][1] += fin[fidx(L, sp, i, jd, 2)];
@@ -757,14 +810,17 @@ __global__ void adj_rev_kappa_kernel(AL L, const double* __restrict__ fin, StepC
       D[e] = v;
     }
     // kappa_in = N rho_in / D, rho_in,s = theta C_s m_s
+    #pragma unroll
     for (int sp = 0; sp < 2; ++sp) *theta_acc += kb[sp] * c.kappa[sp] / L.theta;
   }
   __syncthreads();
   // d kappa / d f(x, j) = -kappa / D * (2 at column 1 (N_x-2), -1 at column 2 (N_x-3))
   for (int jd = t; jd < L.N; jd += blockDim.x)
+    #pragma unroll
     for (int sp = 0; sp < 2; ++sp) {
       const double gi = -kb[sp] * c.kappa[sp] / D[sp];
       const double go = -kb[2 + sp] * c.kappa[2 + sp] / D[2 + sp];
+      #pragma unroll
       for (int i = 0; i < 9; ++i) {
         lamp[fidx(L, sp, i, jd, 1)] += 2.0 * gi;
         lamp[fidx(L, sp, i, jd, 2)] -= gi;
@@ -814,6 +870,7 @@ AL derive_al(const lbm_mix_params* p, int Nx) {
   const double mx_out = Co[0] * L.mh[0] + Co[1] * L.mh[1];
   const double mu = p->Kn_out * p->N * (1.0 / 3.0) / sqrt(kPiD / (6.0 * mx_out));
   const double mu_s[2] = {p->mu_ratio_a * mu, p->mu_ratio_b * mu};
+  #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     L.s[sp] = 1.0 / L.mh[sp];
     L.cw[sp][0] = (9.0 - 5.0 * L.s[sp]) / 9.0;
