@@ -150,6 +150,14 @@ int lbm_mix_moments_device(lbm_mix* h, double* d_out);
 int lbm_mix_separation(lbm_mix* h, double* CL, double* Cl_tilde, double* mdot_a,
                        double* mdot_b, double* Cl_profile, int* x_min);
 
+/* Volume flow Q_v of the mixture through column x (Sec. 4.2, Fig. 7; the
+ * paper gives no formula: read as the sum over the rows of the mixture
+ * velocity u_x = (rho_a u_a,x + rho_b u_b,x)/(rho_a + rho_b) of Eq. rhou,
+ * in lattice units).  x < 0 selects the last updated column N_x - 2 (the
+ * outlet).  Synchronises.  Errors: LBM_EINVAL (x not an updated column),
+ * LBM_ENONFINITE, LBM_ECUDA. */
+int lbm_mix_volume_flow(lbm_mix* h, int x, double* Qv);
+
 /* Copies up to max_records of the most recent diagnostic records, oldest
  * first, into rec[max_records][8] = {record number, CL, C~_l, mdot_a,
  * mdot_b, x_min, total mass a, total mass b}; *count gets the number copied.

@@ -72,6 +72,7 @@ _SIGS = {
     "lbm_mix_moments_device": (_I, [_H, ctypes.c_void_p]),
     "lbm_mix_separation": (_I, [_H, _PD, _PD, _PD, _PD, _PD, ctypes.POINTER(_I)]),
     "lbm_mix_history": (_I, [_H, _PD, _L, ctypes.POINTER(_L)]),
+    "lbm_mix_volume_flow": (_I, [_H, _I, _PD]),
     "lbm_mix_set_accommodation_field": (_I, [_H, _PD, _L]),
     "lbm_mix_set_post_state": (_I, [_H, _PF, _L]),
     "lbm_mix_get_post_state": (_I, [_H, _PF, _L]),
@@ -203,6 +204,12 @@ def lbm_mix_moments(h) -> dict:
 def lbm_mix_moments_device(h, d_out_ptr: int) -> None:
     _check(load().lbm_mix_moments_device(h, ctypes.c_void_p(int(d_out_ptr))),
            "lbm_mix_moments_device")
+
+
+def lbm_mix_volume_flow(h, x: int = -1) -> float:
+    q = _D()
+    _check(load().lbm_mix_volume_flow(h, int(x), ctypes.byref(q)), "lbm_mix_volume_flow")
+    return q.value
 
 
 def lbm_mix_separation(h) -> dict:
@@ -412,6 +419,9 @@ class LbmMix:
 
     def separation(self) -> dict:
         return lbm_mix_separation(self.h)
+
+    def volume_flow(self, x: int = -1) -> float:
+        return lbm_mix_volume_flow(self.h, x)
 
     def history(self, max_records: int = 4096) -> np.ndarray:
         return lbm_mix_history(self.h, max_records)

@@ -38,7 +38,6 @@
 #include <new>
 
 #include "../../include/lbm_mix.h"
-#include "lbm_internal.h"
 
 namespace {
 
@@ -1136,6 +1135,28 @@ __global__ void lbm_convert_kernel(Lat L, ST* __restrict__ f, const float* __res
   }
 }
 
+// Volume flow through column x: sum over the rows of the mixture velocity
+// u_x = (rho_a u_a,x + rho_b u_b,x) / (rho_a + rho_b) of a moments array
+// [6][N][Nx] (rho_a, rho_b, u_a (x, y), u_b (x, y)); one block, fixed order.
+__global__ void lbm_volume_flow_kernel(const double* __restrict__ mom, int N, int Nx, int x,
+                                       double* __restrict__ out) {
+  __shared__ double red[256];
+  const size_t plane = (size_t)N * Nx;
+  double v = 0.0;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const size_t o = (size_t)j * Nx + x;
+    const double ra = mom[o], rb = mom[plane + o];
+    v += (ra * mom[2 * plane + o] + rb * mom[4 * plane + o]) / (ra + rb);
+  }
+  red[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < (int)blockDim.x; ++k) s += red[k];
+    *out = s;
+  }
+}
+
 // Steady-state residual over the column sums: R = |c - c_old| / (K |c|),
 // then c_old = c.  One CTA.
 __global__ void lbm_residual_kernel(const double* __restrict__ c, double* __restrict__ c_old,
@@ -1819,6 +1840,25 @@ int lbm_mix_moments(lbm_mix* h, double* rho_a, double* rho_b, double* ua_x, doub
   return LBM_OK;
 }
 
+int lbm_mix_volume_flow(lbm_mix* h, int x, double* Qv) {
+  int st = check_handle(h);
+  if (st) return st;
+  if (!Qv) return set_err(LBM_EINVAL, "Qv is NULL");
+  if (x < 0) x = h->L.x_periodic ? 0 : h->L.Nx - 2;
+  if (x >= h->L.Nx || (!h->L.x_periodic && (x < 1 || x > h->L.Nx - 2)))
+    return set_err(LBM_EINVAL, "column %d is not an updated column", x);
+  const size_t plane = (size_t)h->L.N * h->L.Nx;
+  if (!h->mom) CK(cudaMalloc((void**)&h->mom, sizeof(double) * 6 * plane));
+  if ((st = launch_moments(h, h->mom))) return st;
+  lbm_volume_flow_kernel<<<1, 256, 0, h->stream>>>(h->mom, h->L.N, h->L.Nx, x, h->resid);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(h->h_pinned, h->resid, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *Qv = h->h_pinned[0];
+  if (!isfinite(*Qv)) return set_err(LBM_ENONFINITE, "non-finite volume flow");
+  return LBM_OK;
+}
+
 int lbm_mix_separation(lbm_mix* h, double* CL, double* Cl_tilde, double* mdot_a, double* mdot_b,
                        double* Cl_profile, int* x_min) {
   int st = check_handle(h);
@@ -2273,6 +2313,8 @@ int lbm_sweep_schedule(lbm_sweep* s, int* policy, int* rows_per_block, double* r
 }  // extern "C"
 
 // ------------------------------------------- helpers for other translation units
+#include "lbm_internal.h"
+
 int lbm_internal_error(int code, const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);

@@ -89,3 +89,29 @@ def sweep_instances(n: int = 96, seed: int = 0) -> list[dict]:
                         C_l=(0.1, 0.3, 0.5, 0.7, 0.9)[k % 5], theta=theta, Kn_out=kn,
                         N=N, L_over_H=LH))
     return out
+
+
+def paper_table1(N: int = 20, L_over_H: float = 35.0) -> list[tuple[str, dict]]:
+    """Every run of the paper's Table 1 on its 20 x 700 lattice: Cases 1-5
+    He-Ar, 6-10 Ne-Ar, with (C_l,in, C_l,out, Kn_out, theta) as listed; the
+    Kn_out and theta lists of Cases 2 and 7 are crossed."""
+    rows = [
+        (1, HE, 0.3, 0.3, (0.3,), (4.0,)),
+        (2, HE, 0.5, 0.5, (0.3, 0.5, 1.0, 3.0, 5.0), (2.0, 3.0, 4.0, 5.0)),
+        (3, HE, 0.7, 0.7, (0.3,), (4.0,)),
+        (4, HE, 0.7, 0.3, (0.3, 1.0), (2.0,)),
+        (5, HE, 0.3, 0.7, (0.3, 1.0), (2.0,)),
+        (6, NE, 0.3, 0.3, (0.3,), (4.0,)),
+        (7, NE, 0.5, 0.5, (0.3, 0.5, 1.0, 3.0, 5.0), (2.0, 3.0, 4.0, 5.0)),
+        (8, NE, 0.7, 0.7, (0.3,), (4.0,)),
+        (9, NE, 0.7, 0.3, (0.3, 1.0), (2.0,)),
+        (10, NE, 0.3, 0.7, (0.3, 1.0), (2.0,)),
+    ]
+    out = []
+    for case, m_a, cin, cout, kns, thetas in rows:
+        for kn in kns:
+            for th in thetas:
+                out.append((f"case{case}_kn{kn:g}_theta{th:g}",
+                            dict(m_a=m_a, m_b=AR, C_l=cin, C_l_out=cout, theta=th, Kn_out=kn,
+                                 N=N, L_over_H=L_over_H)))
+    return out

@@ -296,3 +296,18 @@ def test_neon_argon_full_size_one_step():
     scale = max(np.abs(mo["ua_x"]).max(), np.abs(mo["ub_x"]).max())
     for k in ("ua_x", "ua_y", "ub_x", "ub_y"):
         assert np.abs(mg[k] - mo[k]).max() < RTOL_U * scale + ATOL_U, k
+
+
+def test_volume_flow_matches_oracle():
+    """Q_v (the row sum of the mixture velocity at the outlet column) against
+    the same sum formed from the oracle's moments."""
+    p = workloads.preset("heli_argon_320x16")
+    g, o = _pair(p, 2000)
+    mo = o.moments()
+    x = o.N_x - 2
+    ux = (mo["rho_a"][:, x] * mo["ua_x"][:, x] + mo["rho_b"][:, x] * mo["ub_x"][:, x]) / (
+        mo["rho_a"][:, x] + mo["rho_b"][:, x])
+    q = g.volume_flow()
+    assert abs(q - ux.sum()) < RTOL_U * abs(ux.sum())
+    with pytest.raises(binding.LbmError):
+        g.volume_flow(0)  # the inlet boundary column is not updated
