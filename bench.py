@@ -212,7 +212,7 @@ def run_adjoint(args, stream):
     p = workloads.preset("heli_argon_1280x64")
     nx = workloads.n_x(p)
     alpha = workloads.random_accommodation(nx, 1).reshape(2, nx)
-    steps, ck = 5000, 70
+    steps, ck = args.adjoint_steps, 70
     a = binding.LbmAdjoint(p, steps, ck, alpha, stream=stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -428,6 +428,8 @@ def main():
                     help="skip the BF16/FP16 storage timings")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the adjoint (gradient) timing")
+    ap.add_argument("--adjoint-steps", type=int, default=5000,
+                    help="steps of the adjoint workload (5000 for the sensitivity study)")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the 96-channel parametric sweep")
     ap.add_argument("--sweep-cap", type=int, default=10000,

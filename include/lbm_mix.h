@@ -244,7 +244,7 @@ int lbm_mix_step_noalloc(const lbm_mix_params* p, const float* d_in, float* d_ou
 
 /* Node-to-CTA schedule of h: rows of one strip handled by one CTA of the
  * step kernel, a multiple of 8 (capped at N rounded up to 8); 0 restores the
- * library default (row blocks of at most 128 rows).  Changes only the order
+ * library default (96 rows).  Changes only the order
  * of the FP64 column reductions.  May allocate; not during stream capture.
  * Errors: LBM_EINVAL (bad handle, rows not a multiple of 8), LBM_ENOMEM,
  * LBM_ECUDA. */
@@ -262,8 +262,8 @@ int lbm_mix_set_rows_per_block(lbm_mix* h, int rows);
  * ------------------------------------------------------------------- */
 typedef struct lbm_sweep lbm_sweep;
 
-/* Node-to-CTA schedules the autotuner tries: 0 library default (<= 128 rows
- * per CTA), 1: 64, 2: 32, 3: 16 rows, 4: enough rows per CTA to give each
+/* Node-to-CTA schedules the autotuner tries: 0 library default (96 rows per
+ * CTA), 1: 64, 2: 32, 3: 16 rows, 4: enough rows per CTA to give each
  * instance about two CTAs per SM. */
 #define LBM_SWEEP_NPOLICY 5
 

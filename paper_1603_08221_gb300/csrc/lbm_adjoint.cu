@@ -609,32 +609,36 @@ __global__ void adj_seed_kernel(AL L, int objective, int xs, double Sl, double S
     }
 }
 
-// Reverse of Collide for every node: gbar = (dCollide/dg)^T lam_t; the
-// adjoints of 1/tau_q are summed per column and half, those of ln mu per
-// column (block (32, 8): columns x rows, fixed-order reductions).
-__global__ void adj_rev_node_kernel(AL L, const double* __restrict__ fin,
-                                    const double* __restrict__ lam, StepCols c,
-                                    double* __restrict__ gbar, double* __restrict__ omqbar,
-                                    double* __restrict__ lnmu_col) {
-  __shared__ double red[3][8][32];
+// Reverse of Collide for every node: gbar = (dCollide/dg)^T lam_t.  Block
+// (32, 4) covers 32 columns x REV_ROWS rows, so the grid spreads over all
+// SMs; the adjoints of 1/tau_q (per half) and of ln mu are summed per column
+// within the block and written as per-row-block partials, which
+// adj_rev_tauq_kernel adds up in row-block order.
+constexpr int REV_ROWS = 8;
+__global__ void __launch_bounds__(128) adj_rev_node_kernel(
+    AL L, const double* __restrict__ fin, const double* __restrict__ lam, StepCols c,
+    double* __restrict__ gbar, double* __restrict__ part) {
+  __shared__ double red[3][4][32];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int x = blockIdx.x * 32 + tx;
+  const int j0 = blockIdx.y * REV_ROWS;
+  const int j1 = min(L.N, j0 + REV_ROWS);
   const int half = (L.N + 1) / 2;
   double accq[2] = {0, 0}, accm = 0;
   if (x < L.Nx && interior(L, x)) {
-    for (int j = ty; j < L.N; j += 8) {
+    for (int j = j0 + ty; j < j1; j += 4) {
       double g[2][9], fb[2][9], gb[2][9];
       pull(L, fin, c.r, c.kappa, x, j, g);
-      #pragma unroll
+#pragma unroll
       for (int sp = 0; sp < 2; ++sp)
-        #pragma unroll
+#pragma unroll
         for (int i = 0; i < 9; ++i) fb[sp][i] = lam[fidx(L, sp, i, j, x)];
       const int h = j < half ? 0 : 1;
       double oqb, lmb;
       node_reverse(L, g, j + 0.5, c.omq[h * L.Nx + x], fb, gb, &oqb, &lmb);
-      #pragma unroll
+#pragma unroll
       for (int sp = 0; sp < 2; ++sp)
-        #pragma unroll
+#pragma unroll
         for (int i = 0; i < 9; ++i) gbar[fidx(L, sp, i, j, x)] = gb[sp][i];
       accq[h] += oqb;
       accm += lmb;
@@ -646,31 +650,42 @@ __global__ void adj_rev_node_kernel(AL L, const double* __restrict__ fin,
   __syncthreads();
   if (ty == 0 && x < L.Nx) {
     double a = 0, b = 0, m = 0;
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 4; ++k) {
       a += red[0][k][tx];
       b += red[1][k][tx];
       m += red[2][k][tx];
     }
-    omqbar[x] = a;
-    omqbar[L.Nx + x] = b;
-    lnmu_col[x] += m;
+    double* pb = part + (size_t)blockIdx.y * 3 * L.Nx;
+    pb[x] = a;
+    pb[L.Nx + x] = b;
+    pb[2 * L.Nx + x] = m;
   }
 }
 
 // Reverse of tau_q per column and wall: adds to the wall nodes' gbar, the
-// accommodation adjoint and ln mu.
+// accommodation adjoint and ln mu.  First sums the row-block partials of
+// adj_rev_node_kernel for this column in row-block order.
 __global__ void adj_rev_tauq_kernel(AL L, const double* __restrict__ fin,
                                     const double* __restrict__ alpha, StepCols c,
-                                    const double* __restrict__ omqbar, double* __restrict__ gbar,
-                                    double* __restrict__ alphabar, double* __restrict__ lnmu_col) {
+                                    const double* __restrict__ part, int nparts,
+                                    double* __restrict__ gbar, double* __restrict__ alphabar,
+                                    double* __restrict__ lnmu_col) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= L.Nx || !interior(L, x)) return;
+  double omqbar[2] = {0.0, 0.0}, lm = 0.0;
+  for (int b = 0; b < nparts; ++b) {
+    const double* pb = part + (size_t)b * 3 * L.Nx;
+    omqbar[0] += pb[x];
+    omqbar[1] += pb[L.Nx + x];
+    lm += pb[2 * L.Nx + x];
+  }
+  lnmu_col[x] += lm;
   for (int w = 0; w < 2; ++w) {
     const int jw = w == 0 ? 0 : L.N - 1;
     double g[2][9], gb[2][9] = {};
     pull(L, fin, c.r, c.kappa, x, jw, g);
     const double omq = c.omq[w * L.Nx + x];
-    const double taub = -omqbar[w * L.Nx + x] * omq * omq;  // omq = 1/tau_q
+    const double taub = -omqbar[w] * omq * omq;  // omq = 1/tau_q
     double ab = 0, lmb = 0;
     tau_q(L, g, alpha[w * L.Nx + x], taub, gb, &ab, &lmb);
     #pragma unroll
@@ -910,7 +925,7 @@ struct lbm_adj {
   double* dtheta0 = nullptr;  // d f^0 / d theta
   double* alpha = nullptr;    // [2][Nx]
   double* alphabar = nullptr;
-  double* omqbar = nullptr;   // [2][Nx]
+  double* part_rev = nullptr;  // [ceil(N/REV_ROWS)][3][Nx] row-block partials
   double* lnmu_col = nullptr; // [Nx]
   double* theta_acc = nullptr;  // [1]
   double* colsum = nullptr;   // [3][Nx]
@@ -1016,7 +1031,7 @@ int lbm_adj_create(const lbm_mix_params* p, long nsteps, int checkpoint_every, v
   ALLOCA(a->dtheta0, sizeof(double) * a->S);
   ALLOCA(a->alpha, sizeof(double) * 2 * Nx);
   ALLOCA(a->alphabar, sizeof(double) * 2 * Nx);
-  ALLOCA(a->omqbar, sizeof(double) * 2 * Nx);
+  ALLOCA(a->part_rev, sizeof(double) * 3 * Nx * (size_t)((p->N + REV_ROWS - 1) / REV_ROWS));
   ALLOCA(a->lnmu_col, sizeof(double) * Nx);
   ALLOCA(a->theta_acc, sizeof(double));
   ALLOCA(a->colsum, sizeof(double) * 3 * Nx);
@@ -1059,7 +1074,7 @@ void lbm_adj_destroy(lbm_adj* a) {
   cudaFree(a->dtheta0);
   cudaFree(a->alpha);
   cudaFree(a->alphabar);
-  cudaFree(a->omqbar);
+  cudaFree(a->part_rev);
   cudaFree(a->lnmu_col);
   cudaFree(a->theta_acc);
   cudaFree(a->colsum);
@@ -1150,10 +1165,11 @@ int lbm_adj_gradient(lbm_adj* a, int objective, double* dtheta, double* dkn, dou
       const long k = t - t0 - 1;
       const double* fin = a->seg + a->S * (size_t)k;
       StepCols c = cols_of(a, a->segcols + cw * k);
-      adj_rev_node_kernel<<<(L.Nx + 31) / 32, dim3(32, 8), 0, a->stream>>>(
-          L, fin, a->lam[cur], c, a->gbar, a->omqbar, a->lnmu_col);
-      adj_rev_tauq_kernel<<<cb, 128, 0, a->stream>>>(L, fin, a->alpha, c, a->omqbar, a->gbar,
-                                                     a->alphabar, a->lnmu_col);
+      const int nparts = (L.N + REV_ROWS - 1) / REV_ROWS;
+      adj_rev_node_kernel<<<dim3((L.Nx + 31) / 32, nparts), dim3(32, 4), 0, a->stream>>>(
+          L, fin, a->lam[cur], c, a->gbar, a->part_rev);
+      adj_rev_tauq_kernel<<<cb, 128, 0, a->stream>>>(L, fin, a->alpha, c, a->part_rev, nparts,
+                                                     a->gbar, a->alphabar, a->lnmu_col);
       adj_rev_pull_kernel<<<grd, 128, 0, a->stream>>>(L, fin, a->alpha, c, a->gbar,
                                                       a->lam[1 - cur], a->alphabar);
       adj_rev_kappa_kernel<<<1, 256, 0, a->stream>>>(L, fin, c, a->gbar, a->lam[1 - cur],
