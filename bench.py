@@ -8,8 +8,10 @@ i.e. one launch of the fused kernel over the Ne-Ar 32768 x 512 channel
 (16.8 M nodes, two species, 2.4 GB of FP32 populations: larger than L2, so no
 flush is needed between steps).
 
-Prints ONE JSON line (rank 0).  --impl reference times the FP64 oracle on
-the host cores instead.
+Prints ONE JSON line (rank 0).  Beside the FP32 line it carries the BF16 /
+FP16 storage timings, the 96-channel parametric sweep against sequential
+lone runs, and the adjoint (gradient) time against the forward time.
+--impl reference times the FP64 oracle on the host cores instead.
 """
 from __future__ import annotations
 

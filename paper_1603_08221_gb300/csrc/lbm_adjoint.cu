@@ -62,22 +62,26 @@ struct AL {
 
 // ------------------------------------------------ special functions (FP64)
 // 1/k for the series below (multiplications instead of FP64 divisions).
-__constant__ double kInvK[48] = {
-    0.0,       1.0,       1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,  1.0 / 7,
-    1.0 / 8,   1.0 / 9,   1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15,
-    1.0 / 16,  1.0 / 17,  1.0 / 18, 1.0 / 19, 1.0 / 20, 1.0 / 21, 1.0 / 22, 1.0 / 23,
-    1.0 / 24,  1.0 / 25,  1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29, 1.0 / 30, 1.0 / 31,
-    1.0 / 32,  1.0 / 33,  1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39,
-    1.0 / 40,  1.0 / 41,  1.0 / 42, 1.0 / 43, 1.0 / 44, 1.0 / 45, 1.0 / 46, 1.0 / 47};
+__constant__ double kInvK[64] = {
+         0.0,  1.0 / 1,  1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,  1.0 / 7,
+     1.0 / 8,  1.0 / 9, 1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15,
+    1.0 / 16, 1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20, 1.0 / 21, 1.0 / 22, 1.0 / 23,
+    1.0 / 24, 1.0 / 25, 1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29, 1.0 / 30, 1.0 / 31,
+    1.0 / 32, 1.0 / 33, 1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39,
+    1.0 / 40, 1.0 / 41, 1.0 / 42, 1.0 / 43, 1.0 / 44, 1.0 / 45, 1.0 / 46, 1.0 / 47,
+    1.0 / 48, 1.0 / 49, 1.0 / 50, 1.0 / 51, 1.0 / 52, 1.0 / 53, 1.0 / 54, 1.0 / 55,
+    1.0 / 56, 1.0 / 57, 1.0 / 58, 1.0 / 59, 1.0 / 60, 1.0 / 61, 1.0 / 62, 1.0 / 63};
 
-// E_1 from its power series for x <= 3 (A&S 5.1.11: at x = 3 the series'
-// cancellation costs ~2.5 digits, leaving ~4e-14 relative) and its continued
-// fraction for x > 3 (A&S 5.1.22, modified Lentz, which converges in a few
-// tens of terms there); both loops are bounded.
+// E_1 from its power series for x <= 8 (A&S 5.1.11; at most 45 terms, and
+// the series' cancellation leaves a relative error below 5e-10 at x = 8,
+// i.e. below 1.1e-12 absolute in psi = ... - x^2 E_1 and in psi') and its
+// continued fraction for x > 8 (A&S 5.1.22, modified Lentz, a dozen terms
+// there).  The series needs no FP64 division, the slow path of this part.
+// Both loops are bounded.
 __device__ double e1d(double x) {
-  if (x <= 3.0) {
+  if (x <= 8.0) {
     double t = 1.0, s = 0.0;
-    for (int k = 1; k < 48; ++k) {
+    for (int k = 1; k < 64; ++k) {
       t *= -x * kInvK[k];
       const double d = t * kInvK[k];
       s += d;
