@@ -150,6 +150,25 @@ int lbm_mix_moments_device(lbm_mix* h, double* d_out);
 int lbm_mix_separation(lbm_mix* h, double* CL, double* Cl_tilde, double* mdot_a,
                        double* mdot_b, double* Cl_profile, int* x_min);
 
+/* Device pointers of the handle's current state, for zero-copy views (e.g.
+ * torch tensors through __cuda_array_interface__); each output nullable:
+ *   populations    the latest post-collision populations as stored: deviations
+ *                  d = f - w_i alpha_si rhobar_s(x) from the rest equilibrium
+ *                  (Eq. feq, u = 0), element type of the storage (float, or
+ *                  2-byte BF16/FP16), strip layout
+ *                  index = (x/32) * 576 N + j * 576 + i * 64 + 2 * (x%32) + sigma,
+ *                  *n_populations elements (18 * N * 32 * ceil(N_x/32));
+ *   refrho         rhobar_s(x), float [2][N_x];
+ *   alpha          accommodation coefficients, float [2][N_x] (bottom, top);
+ *   colsum         FP64 [4][N_x] column sums of the latest diagnostic step
+ *                  (sum_j rho_a, sum_j rho_b, and the species x momenta).
+ * The pointers stay owned by the handle and are valid until the next call
+ * that steps, re-references, initialises or uploads a state (the two
+ * population buffers alternate).  Reading them must be ordered after the
+ * handle's stream.  No counterpart in the paper. */
+int lbm_mix_device_ptrs(lbm_mix* h, void** populations, long* n_populations, void** refrho,
+                        void** alpha, void** colsum);
+
 /* Volume flow Q_v of the mixture through column x (Sec. 4.2, Fig. 7; the
  * paper gives no formula: read as the sum over the rows of the mixture
  * velocity u_x = (rho_a u_a,x + rho_b u_b,x)/(rho_a + rho_b) of Eq. rhou,

@@ -73,6 +73,9 @@ _SIGS = {
     "lbm_mix_separation": (_I, [_H, _PD, _PD, _PD, _PD, _PD, ctypes.POINTER(_I)]),
     "lbm_mix_history": (_I, [_H, _PD, _L, ctypes.POINTER(_L)]),
     "lbm_mix_volume_flow": (_I, [_H, _I, _PD]),
+    "lbm_mix_device_ptrs": (_I, [_H, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_L),
+                                 ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                 ctypes.POINTER(ctypes.c_void_p)]),
     "lbm_mix_set_accommodation_field": (_I, [_H, _PD, _L]),
     "lbm_mix_set_post_state": (_I, [_H, _PF, _L]),
     "lbm_mix_get_post_state": (_I, [_H, _PF, _L]),
@@ -204,6 +207,27 @@ def lbm_mix_moments(h) -> dict:
 def lbm_mix_moments_device(h, d_out_ptr: int) -> None:
     _check(load().lbm_mix_moments_device(h, ctypes.c_void_p(int(d_out_ptr))),
            "lbm_mix_moments_device")
+
+
+def lbm_mix_device_ptrs(h) -> dict:
+    pop, refrho, alpha, cs = (ctypes.c_void_p() for _ in range(4))
+    n = _L()
+    _check(load().lbm_mix_device_ptrs(h, ctypes.byref(pop), ctypes.byref(n), ctypes.byref(refrho),
+                                      ctypes.byref(alpha), ctypes.byref(cs)),
+           "lbm_mix_device_ptrs")
+    return {"populations": pop.value, "n_populations": n.value, "refrho": refrho.value,
+            "alpha": alpha.value, "colsum": cs.value}
+
+
+class _DeviceArray:
+    """A CUDA array interface (version 3) over library-owned device memory,
+    so that torch.as_tensor (or any consumer of the interface) views it
+    without a copy."""
+
+    def __init__(self, ptr: int, shape: tuple, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
 
 
 def lbm_mix_volume_flow(h, x: int = -1) -> float:
@@ -422,6 +446,21 @@ class LbmMix:
 
     def volume_flow(self, x: int = -1) -> float:
         return lbm_mix_volume_flow(self.h, x)
+
+    def device_views(self) -> dict:
+        """Zero-copy CUDA array interfaces of the current state (valid until
+        the next step): populations (stored deviations, strip layout, storage
+        type), refrho and alpha (float [2][N_x]) and the column sums (FP64
+        [4][N_x]).  Pass each to torch.as_tensor(..., device='cuda').  BF16
+        populations appear as raw 16-bit words (the interface has no
+        bfloat16 type): view them with .view(torch.bfloat16)."""
+        d = lbm_mix_device_ptrs(self.h)
+        st = self.params.storage
+        typestr = "<f4" if st == LBM_FP32 else "<f2" if st == LBM_FP16 else "<u2"
+        return {"populations": _DeviceArray(d["populations"], (d["n_populations"],), typestr),
+                "refrho": _DeviceArray(d["refrho"], (2, self.N_x), "<f4"),
+                "alpha": _DeviceArray(d["alpha"], (2, self.N_x), "<f4"),
+                "colsum": _DeviceArray(d["colsum"], (4, self.N_x), "<f8")}
 
     def history(self, max_records: int = 4096) -> np.ndarray:
         return lbm_mix_history(self.h, max_records)

@@ -1846,6 +1846,18 @@ int lbm_mix_moments(lbm_mix* h, double* rho_a, double* rho_b, double* ua_x, doub
   return LBM_OK;
 }
 
+int lbm_mix_device_ptrs(lbm_mix* h, void** populations, long* n_populations, void** refrho,
+                        void** alpha, void** colsum) {
+  int st = check_handle(h);
+  if (st) return st;
+  if (populations) *populations = h->buf[h->cur];
+  if (n_populations) *n_populations = 18L * h->L.N * h->L.pitch;
+  if (refrho) *refrho = h->refrho;
+  if (alpha) *alpha = h->alpha;
+  if (colsum) *colsum = h->cs[h->cur];
+  return LBM_OK;
+}
+
 int lbm_mix_volume_flow(lbm_mix* h, int x, double* Qv) {
   int st = check_handle(h);
   if (st) return st;

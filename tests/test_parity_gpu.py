@@ -311,3 +311,30 @@ def test_volume_flow_matches_oracle():
     assert abs(q - ux.sum()) < RTOL_U * abs(ux.sum())
     with pytest.raises(binding.LbmError):
         g.volume_flow(0)  # the inlet boundary column is not updated
+
+
+def test_device_views_are_the_state():
+    """Zero-copy views of the device state (lbm_mix_device_ptrs): the stored
+    deviations plus the rest equilibrium of the reference density give the
+    post-collision populations the library reports."""
+    torch = pytest.importorskip("torch")
+    p = workloads.preset("heli_argon_320x16", N=16, N_x=100)
+    g = binding.LbmMix(**p)
+    g.init()
+    g.step(37)
+    F = g.get_post_state_f64()
+    v = g.device_views()
+    d = torch.as_tensor(v["populations"], device="cuda").double().cpu().numpy()
+    rb = torch.as_tensor(v["refrho"], device="cuda").double().cpu().numpy()
+    al = torch.as_tensor(v["alpha"], device="cuda").cpu().numpy()
+    N, Nx = 16, 100
+    S = (Nx + 31) // 32
+    dev = d.reshape(S, N, 9, 32, 2).transpose(4, 2, 1, 0, 3).reshape(2, 9, N, S * 32)[..., :Nx]
+    m_min = min(p["m_a"], p["m_b"])
+    w = np.zeros((2, 9))
+    for sp, m in enumerate((p["m_a"], p["m_b"])):
+        s = float(np.float32(m_min / m))
+        w[sp] = [np.float32((9 - 5 * s) / 9)] + [np.float32(s / 9)] * 4 + [np.float32(s / 36)] * 4
+    G = dev + w[:, :, None, None] * rb[:, None, None, :]
+    assert np.abs(G[..., 1:-1] - F[..., 1:-1]).max() < 1e-6 * np.abs(F).max()
+    assert np.all(al == np.float32(p.get("accommodation", 1.0)))
