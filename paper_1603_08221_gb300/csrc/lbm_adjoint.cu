@@ -471,17 +471,32 @@ __device__ double dbb_r(const AL& L, const double* f, int x, int j, double alpha
 }
 
 // ------------------------------------------------------------ kernels
+// Sum of v over a block of 256 threads, in a fixed tree order (warp
+// shuffles, then the eight warp sums); every thread receives the total.
+__device__ double block_sum256(double v, double* sm /* [8] */) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();  // sm may still be read from a previous call
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t += sm[k];
+  return t;
+}
+
 // kappa of both ends (Eq. rho2) from the column sums of columns 1, 2 and
 // N_x - 2, N_x - 3 of f; one block.
-__global__ void adj_kappa_kernel(AL L, const double* __restrict__ f, double* __restrict__ kap) {
-  __shared__ double red[4][2][256];  // [end * 2 + species][column 1 or 2 of the end][thread]
+__global__ void __launch_bounds__(256) adj_kappa_kernel(AL L, const double* __restrict__ f,
+                                                        double* __restrict__ kap) {
+  __shared__ double sm[8];
   const int t = threadIdx.x;
   double acc[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
   if (!L.x_periodic) {
     for (int j = t; j < L.N; j += blockDim.x)
-      #pragma unroll
+#pragma unroll
       for (int sp = 0; sp < 2; ++sp)
-        #pragma unroll
+#pragma unroll
         for (int i = 0; i < 9; ++i) {
           acc[sp][0] += f[fidx(L, sp, i, j, 1)];
           acc[sp][1] += f[fidx(L, sp, i, j, 2)];
@@ -490,19 +505,11 @@ __global__ void adj_kappa_kernel(AL L, const double* __restrict__ f, double* __r
         }
   }
   for (int e = 0; e < 4; ++e) {
-    red[e][0][t] = acc[e][0];
-    red[e][1][t] = acc[e][1];
-  }
-  __syncthreads();
-  if (t == 0) {
-    for (int e = 0; e < 4; ++e) {
-      double c1 = 0, c2 = 0;
-      for (int k = 0; k < (int)blockDim.x; ++k) {
-        c1 += red[e][0][k];
-        c2 += red[e][1][k];
-      }
+    // column sums enter as 2 c(1) - c(2) (resp. N_x - 2, N_x - 3)
+    const double D = block_sum256(2.0 * acc[e][0] - acc[e][1], sm);
+    if (t == 0) {
       const double target = e < 2 ? L.rho_in[e] : L.rho_out[e - 2];
-      kap[e] = L.x_periodic ? 1.0 : L.N * target / (2.0 * c1 - c2);
+      kap[e] = L.x_periodic ? 1.0 : L.N * target / D;
     }
   }
 }
@@ -780,18 +787,17 @@ __global__ void adj_rev_pull_kernel(AL L, const double* __restrict__ fin,
 // kappa adjoints (reduced over the end columns' rows), their terms in
 // lam_prev at columns 1, 2 and N_x - 2, N_x - 3, and the theta adjoint of
 // rho_in; one block, fixed order.
-__global__ void adj_rev_kappa_kernel(AL L, const double* __restrict__ fin, StepCols c,
-                                     const double* __restrict__ gbar, double* __restrict__ lamp,
-                                     double* __restrict__ theta_acc) {
-  __shared__ double red[4][256];
-  __shared__ double kb[4], D[4];
+__global__ void __launch_bounds__(256) adj_rev_kappa_kernel(
+    AL L, const double* __restrict__ fin, StepCols c, const double* __restrict__ gbar,
+    double* __restrict__ lamp, double* __restrict__ theta_acc) {
+  __shared__ double sm[8];
   const int t = threadIdx.x;
   if (L.x_periodic) return;
   double acc[4] = {0, 0, 0, 0}, cs[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
   for (int jd = t; jd < L.N; jd += blockDim.x)
-    #pragma unroll
+#pragma unroll
     for (int sp = 0; sp < 2; ++sp) {
-      #pragma unroll
+#pragma unroll
       for (int i = 0; i < 9; ++i) {
         const int js = jd - CYd[i];
         if (js < 0 || js >= L.N) continue;
@@ -803,7 +809,7 @@ __global__ void adj_rev_kappa_kernel(AL L, const double* __restrict__ fin, StepC
                          (2.0 * fin[fidx(L, sp, i, js, L.Nx - 2)] -
                           fin[fidx(L, sp, i, js, L.Nx - 3)]);
       }
-      #pragma unroll
+#pragma unroll
       for (int i = 0; i < 9; ++i) {
         cs[sp][0] += fin[fidx(L, sp, i, jd, 1)];
         cs[sp][1] += fin[fidx(L, sp, i, jd, 2)];
@@ -811,35 +817,21 @@ __global__ void adj_rev_kappa_kernel(AL L, const double* __restrict__ fin, StepC
         cs[2 + sp][1] += fin[fidx(L, sp, i, jd, L.Nx - 3)];
       }
     }
-  for (int e = 0; e < 4; ++e) red[e][t] = acc[e];
-  __syncthreads();
-  if (t == 0)
-    for (int e = 0; e < 4; ++e) {
-      double v = 0;
-      for (int k = 0; k < (int)blockDim.x; ++k) v += red[e][k];
-      kb[e] = v;
-    }
-  __syncthreads();
-  for (int e = 0; e < 4; ++e) red[e][t] = 2.0 * cs[e][0] - cs[e][1];
-  __syncthreads();
-  if (t == 0) {
-    for (int e = 0; e < 4; ++e) {
-      double v = 0;
-      for (int k = 0; k < (int)blockDim.x; ++k) v += red[e][k];
-      D[e] = v;
-    }
-    // kappa_in = N rho_in / D, rho_in,s = theta C_s m_s
-    #pragma unroll
-    for (int sp = 0; sp < 2; ++sp) *theta_acc += kb[sp] * c.kappa[sp] / L.theta;
+  double kb[4], D[4];
+  for (int e = 0; e < 4; ++e) {
+    kb[e] = block_sum256(acc[e], sm);
+    D[e] = block_sum256(2.0 * cs[e][0] - cs[e][1], sm);
   }
-  __syncthreads();
+  // kappa_in = N rho_in / D, rho_in,s = theta C_s m_s
+  if (t == 0)
+    for (int sp = 0; sp < 2; ++sp) *theta_acc += kb[sp] * c.kappa[sp] / L.theta;
   // d kappa / d f(x, j) = -kappa / D * (2 at column 1 (N_x-2), -1 at column 2 (N_x-3))
   for (int jd = t; jd < L.N; jd += blockDim.x)
-    #pragma unroll
+#pragma unroll
     for (int sp = 0; sp < 2; ++sp) {
       const double gi = -kb[sp] * c.kappa[sp] / D[sp];
       const double go = -kb[2 + sp] * c.kappa[2 + sp] / D[2 + sp];
-      #pragma unroll
+#pragma unroll
       for (int i = 0; i < 9; ++i) {
         lamp[fidx(L, sp, i, jd, 1)] += 2.0 * gi;
         lamp[fidx(L, sp, i, jd, 2)] -= gi;
