@@ -338,3 +338,16 @@ def test_device_views_are_the_state():
     G = dev + w[:, :, None, None] * rb[:, None, None, :]
     assert np.abs(G[..., 1:-1] - F[..., 1:-1]).max() < 1e-6 * np.abs(F).max()
     assert np.all(al == np.float32(p.get("accommodation", 1.0)))
+
+
+def test_zero_steps_leave_the_initial_state():
+    """lbm_mix_step(0) is a no-op; the moments of the initial state (no
+    stream yet) equal the oracle's initial moments."""
+    p = workloads.preset("heli_argon_320x16", N=8, N_x=40)
+    g, o = _pair(p, 0)
+    g.step(0)
+    assert g.steps == 0
+    _check_moments(g, o)
+    F = g.get_post_state_f64()
+    Fo = o.get_post_state()
+    assert _relerr(F[..., 1:-1], Fo[..., 1:-1]) < RTOL_RHO

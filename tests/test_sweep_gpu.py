@@ -121,3 +121,12 @@ def test_sweep_reports_a_diverging_instance():
     steps, R, status = sw.run_to_steady(1e-7, 40000, 500)
     assert status[0] == binding.LBM_ENONFINITE and steps[0] <= 2000
     assert status[1] == binding.LBM_OK
+
+
+def test_sweep_with_no_steps():
+    sw = binding.LbmSweep(SMALL[:2])
+    sw.init()
+    steps, R, status = sw.run_to_steady(1e-7, 0, 500)
+    assert steps == [0, 0] and status == [binding.LBM_ENOTCONVERGED] * 2
+    with pytest.raises(binding.LbmError):
+        sw.run_to_steady(1e-7, 1000, 501)  # odd check interval: no whole graphs
