@@ -206,3 +206,33 @@ def test_helium_argon_1280x64_5000_steps():
         d = (H_FD * v).reshape(al.shape)
         fd = (_J(p, al + d, steps, 1, steps) - _J(p, al - d, steps, 1, steps)) / (2 * H_FD)
         assert _close(float(gf @ v), fd, flux)
+
+
+@pytest.mark.parametrize("obj", [binding.LBM_ADJ_CL, binding.LBM_ADJ_FLUX])
+def test_gradient_against_the_complex_step_reference(obj):
+    """Against exact derivatives of the oracle-side complex-step restatement
+    of the time integration (no finite-difference noise): theta, Kn_out,
+    three accommodation components and two random directions, to 1e-8."""
+    from oracle import complex_step as cs
+    al = _alpha(SMALL["N_x"])
+    a = binding.LbmAdjoint(SMALL, STEPS, CKPT, al)
+    a.forward()
+    g = a.gradient(obj)
+    k = 0 if obj == binding.LBM_ADJ_CL else 1
+
+    def ref(**kw):
+        return cs.run(SMALL, STEPS, al, **kw)[2 + k]
+
+    assert _rel(g["theta"], ref(d_theta=1.0)) < 1e-8
+    assert _rel(g["Kn_out"], ref(d_kn=1.0)) < 1e-8
+    rng = np.random.default_rng(5)
+    flat = g["alpha"].ravel()
+    scale = np.abs(flat).max()
+    for idx in rng.choice(flat.size, 3, replace=False):
+        d = np.zeros(flat.size)
+        d[idx] = 1.0
+        r = ref(d_alpha=d.reshape(al.shape))
+        assert abs(flat[idx] - r) <= 1e-8 * abs(r) + 1e-12 * scale, (idx, flat[idx], r)
+    for _ in range(2):
+        v = rng.standard_normal(flat.size)
+        assert _rel(float(flat @ v), ref(d_alpha=v.reshape(al.shape))) < 1e-8
