@@ -93,6 +93,7 @@ def _load():
             "orc_steps": (ctypes.c_long, [_P]),
             "orc_Nx": (ctypes.c_int, [_P]),
             "orc_num_threads": (ctypes.c_int, []),
+            "orc_set_num_threads": (None, [ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -155,6 +156,11 @@ def matrix_Minv() -> np.ndarray:
 
 def num_threads() -> int:
     return _load().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops; n < 1 restores the default."""
+    _load().orc_set_num_threads(int(n))
 
 
 _DEFAULTS = dict(C_l_out=-1.0, accommodation=1.0, c_m0=1.016, tau_rho=1.0,

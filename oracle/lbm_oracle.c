@@ -808,3 +808,15 @@ int orc_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Threads of the OpenMP loops from now on (for timing the oracle on one
+ * core); n < 1 restores the runtime's default. */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  static int dflt = 0;
+  if (!dflt) dflt = omp_get_max_threads();
+  omp_set_num_threads(n >= 1 ? n : dflt);
+#else
+  (void)n;
+#endif
+}
