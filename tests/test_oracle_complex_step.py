@@ -56,3 +56,18 @@ def test_derivatives_match_central_differences_of_the_c_oracle(alpha, what):
     eps = np.finfo(float).eps
     assert abs(dCL - fd_cl) <= 1e-6 * abs(fd_cl) + 64 * eps / h
     assert abs(dfl - fd_fl) <= 1e-6 * abs(fd_fl) + 64 * eps * abs(fp) / h
+
+
+def test_real_part_with_unequal_end_compositions():
+    """C_l,in != C_l,out (as in Cases 4, 5, 9, 10 of Table 1) with an
+    accommodation field, on a 120 x 10 channel at theta = 1.5 (shorter
+    channels with unequal ends diverge in both): the restatement and the C
+    oracle stay equal."""
+    oracle.build()
+    p = dict(P, C_l=0.5, C_l_out=0.3, theta=1.5, Kn_out=0.1, N=10, N_x=120)
+    al = workloads.random_accommodation(120, seed=1, spread=0.05).reshape(2, 120)
+    CL, fl, _, _, F = cs.run(p, 400, al)
+    CLo, flo, Fo = _c_oracle(p, al, 400)
+    assert np.isfinite(Fo).all()
+    assert np.abs(F[..., 1:-1] - Fo[..., 1:-1]).max() < 1e-13 * np.abs(Fo).max()
+    assert abs(CL - CLo) < 1e-13
