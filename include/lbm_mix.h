@@ -218,9 +218,9 @@ int lbm_mix_sync(lbm_mix* h);
 int lbm_mix_eval_special(const double* x, double* e1, double* psi, long n);
 
 /* One time step with no device allocation, for callers that cannot call
- * cudaMalloc (for example code that owns a fixed device-memory budget, runs
- * under an allocator it does not control, or must not allocate while a CUDA
- * graph it belongs to is being captured).  This entry point has no
+ * cudaMalloc (for example code that owns a fixed device-memory budget that
+ * is already handed out, or runs under an allocator it does not control and
+ * may not bypass).  This entry point has no
  * counterpart in the paper; it runs the same fused step kernel as
  * lbm_mix_step, with the kernel's scratch (per-strip partial sums and the
  * arrival tickets of its two-level reduction) in a static device array of
