@@ -348,7 +348,9 @@ typedef struct lbm_adj lbm_adj;
 #define LBM_ADJ_CL 0
 #define LBM_ADJ_FLUX 1
 
-/* Validates p like lbm_mix_create (storage is ignored: FP64) and allocates
+/* Validates p like lbm_mix_create (storage is ignored: FP64; x_periodic
+ * channels are rejected: the adjoint covers the pressure-driven channel with
+ * its inlet and outlet, Eqs. rho1 and rho2) and allocates
  * the checkpoints (ceil(nsteps/checkpoint_every) + 1 states of 18 N N_x
  * doubles) and one interval of replayed states.  stream: cudaStream_t or
  * NULL for an own stream.  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */

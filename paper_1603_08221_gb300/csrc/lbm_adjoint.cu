@@ -994,7 +994,8 @@ int lbm_adj_create(const lbm_mix_params* p, long nsteps, int checkpoint_every, v
   if (st) return st;
   if (nsteps < 1 || checkpoint_every < 1)
     return lbm_internal_error(LBM_EINVAL, "need nsteps >= 1 and checkpoint_every >= 1");
-  if (!p->x_periodic && Nx < 4) return lbm_internal_error(LBM_EINVAL, "need N_x >= 4");
+  if (p->x_periodic)
+    return lbm_internal_error(LBM_EINVAL, "the adjoint covers channels with pressure ends only");
   lbm_adj* a = new (std::nothrow) lbm_adj;
   if (!a) return lbm_internal_error(LBM_ENOMEM, "host allocation failed");
   a->p = *p;

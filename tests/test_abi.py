@@ -113,3 +113,16 @@ def test_sweep_rejects_bad_instances_without_gpu(lib):
     assert "instance 1" in binding.lbm_mix_last_error() or "FP32" in binding.lbm_mix_last_error()
     s = ctypes.c_void_p()
     assert lib.lbm_sweep_create(None, 0, ctypes.byref(s)) == binding.LBM_EINVAL
+
+
+def test_adjoint_rejects_bad_arguments_without_gpu(lib):
+    p = binding.lbm_mix_default_params()
+    a = ctypes.c_void_p()
+    for field, value in (("x_periodic", 1), ("theta", 0.5)):
+        q = binding.lbm_mix_default_params()
+        setattr(q, field, value)
+        assert lib.lbm_adj_create(ctypes.byref(q), 100, 10, None, ctypes.byref(a)) == \
+            binding.LBM_EINVAL
+        assert a.value is None
+    assert lib.lbm_adj_create(ctypes.byref(p), 0, 10, None, ctypes.byref(a)) == binding.LBM_EINVAL
+    assert lib.lbm_adj_create(ctypes.byref(p), 100, 0, None, ctypes.byref(a)) == binding.LBM_EINVAL
