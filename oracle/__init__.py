@@ -7,7 +7,9 @@ imports, links or falls back to it, and the two share no code.
 The arithmetic lives in ``lbm_oracle.c`` (plain C, FP64, one OpenMP loop over
 columns); this module compiles it with gcc and wraps it with ctypes.
 ``complex_step.py`` restates the same time integration in numpy on complex
-numbers, for exact reference derivatives (complex step).
+numbers, for exact reference derivatives (complex step);
+``reference_adjoint.py`` restates it with PyTorch CPU operations for a
+reverse-mode reference gradient (torch.autograd).
 """
 from __future__ import annotations
 

@@ -236,3 +236,20 @@ def test_gradient_against_the_complex_step_reference(obj):
     for _ in range(2):
         v = rng.standard_normal(flat.size)
         assert _rel(float(flat @ v), ref(d_alpha=v.reshape(al.shape))) < 1e-8
+
+
+@pytest.mark.parametrize("obj,name", [(binding.LBM_ADJ_CL, "CL"), (binding.LBM_ADJ_FLUX, "flux")])
+def test_whole_gradient_against_the_reverse_mode_reference(obj, name):
+    """The full accommodation gradient (2 x 40 values), dJ/dtheta and
+    dJ/dKn_out against the oracle-side reverse-mode reference (PyTorch CPU
+    autograd over a restatement of the time integration), to 1e-8."""
+    pytest.importorskip("torch")
+    from oracle import reference_adjoint as ra
+    steps = 100
+    al = _alpha(SMALL["N_x"])
+    a = binding.LbmAdjoint(SMALL, steps, CKPT, al)
+    a.forward()
+    g = a.gradient(obj)
+    J, dth, dkn, dal = ra.gradient(SMALL, steps, al, name)
+    assert _rel(g["theta"], dth) < 1e-8 and _rel(g["Kn_out"], dkn) < 1e-8
+    assert np.abs(g["alpha"] - dal).max() <= 1e-8 * np.abs(dal).max()
