@@ -881,7 +881,6 @@ AL derive_al(const lbm_mix_params* p, int Nx) {
   const double mx_out = Co[0] * L.mh[0] + Co[1] * L.mh[1];
   const double mu = p->Kn_out * p->N * (1.0 / 3.0) / sqrt(kPiD / (6.0 * mx_out));
   const double mu_s[2] = {p->mu_ratio_a * mu, p->mu_ratio_b * mu};
-  #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     L.s[sp] = 1.0 / L.mh[sp];
     L.cw[sp][0] = (9.0 - 5.0 * L.s[sp]) / 9.0;
