@@ -95,6 +95,18 @@ typedef struct {
   double mu_ratio_a, mu_ratio_b;
   int x_periodic; /* test mode: periodic in x, no pressure ends */
   int y_periodic; /* test mode: periodic in y, no walls */
+  /* Readings knobs (0 = the default reading everywhere):
+   *  psi_off   1: Psi = 1 (unbounded mean free path, no wall-confinement
+   *             correction), so tau'_s(0) = 0 in Eq. taoq (test mode);
+   *  r_mode    Eq. R: 0 first printed form, one r for both species with
+   *             sqrt(pi m_x / (6 m_min)); 1 species form sqrt(pi m_x /
+   *             (6 m_sigma)); 2 second printed form with m_r = m_sigma/m_x
+   *             and masses in units of m_min, sqrt(pi m_x^2 / (6 m_sigma));
+   *  lam_mode  lambda_sigma: 0 with the partial pressure p_sigma = x_sigma p;
+   *             1 with the mixture pressure p. */
+  int psi_off;
+  int r_mode;
+  int lam_mode;
 } orc_params;
 
 typedef struct {
@@ -307,16 +319,17 @@ static void node_moments(const orc_sim *S, const double fa[Q], const double fb[Q
    * after Eq. EQFrsp), with the partial pressure for each species */
   ns->lam = S->mu / ns->p * sqrt(PI * S->kT / (2.0 * ns->mx));
   for (int sp = 0; sp < 2; ++sp) {
-    double p_s = ns->x_s[sp] * ns->p;
+    double p_s = S->p.lam_mode == 1 ? ns->p : ns->x_s[sp] * ns->p;
     ns->lam_s[sp] = S->mu_s[sp] / p_s * sqrt(PI * S->kT / (2.0 * S->mh[sp]));
   }
   const double H = (double)S->N;
   const double y = j + 0.5; /* wall at j = 1/2 of the 1-based row index */
+  const int po = S->p.psi_off;
   /* Eq. taos (m_min = 1) */
-  ns->tau_s = 0.5 + ns->lam * orc_Psi(y, H, ns->lam) * sqrt(6.0 / (PI * ns->mx));
+  ns->tau_s = 0.5 + ns->lam * (po ? 1.0 : orc_Psi(y, H, ns->lam)) * sqrt(6.0 / (PI * ns->mx));
   /* Eq. EQFrsp with effective species mean free paths */
-  double lae = ns->lam_s[0] * orc_Psi(y, H, ns->lam_s[0]);
-  double lbe = ns->lam_s[1] * orc_Psi(y, H, ns->lam_s[1]);
+  double lae = ns->lam_s[0] * (po ? 1.0 : orc_Psi(y, H, ns->lam_s[0]));
+  double lbe = ns->lam_s[1] * (po ? 1.0 : orc_Psi(y, H, ns->lam_s[1]));
   double m0 = S->mh[0] + S->mh[1];
   double bracket = 1.0 / sqrt(ns->x_s[0] * lae) + 1.0 / sqrt(ns->x_s[1] * lbe);
   ns->tau_d = 0.5 + 1.5 * sqrt(3.0 * m0 * S->mh[0] * S->mh[1] / (1.0 * ns->mx * ns->mx)) /
@@ -324,15 +337,16 @@ static void node_moments(const orc_sim *S, const double fa[Q], const double fb[Q
 }
 
 /* tau_q of Eq. taoq from a wall node's mixture mean free path, m_x and
- * accommodation coefficient alpha (Eq. A12); dx = 1, H = N. */
-double orc_tau_q(double lam_w, double mx_w, double alpha, double H) {
+ * accommodation coefficient alpha (Eq. A12); dx = 1, H = N.  psi_off: Psi = 1
+ * (no wall-confinement correction), so tau_s is uniform and tau'_s(0) = 0. */
+static double tau_q_of(double lam_w, double mx_w, double alpha, double H, int psi_off) {
   const double vs = sqrt(PI / 6.0); /* varsigma */
   const double g = sqrt(6.0 / (PI * mx_w));
   /* tilde tau_s(0) = tau_s(0) - 1/2 with Psi(0) = psi(H/lambda)/2 */
-  double tt = lam_w * orc_Psi(0.0, H, lam_w) * g;
+  double tt = lam_w * (psi_off ? 1.0 : orc_Psi(0.0, H, lam_w)) * g;
   /* tau'_s(0) = d tilde tau_s / dy at y = 0
    *           = (g/2) [psi'(0) - psi'(H/lambda)] */
-  double dtt = 0.5 * g * (orc_dpsi(0.0) - orc_dpsi(H / lam_w));
+  double dtt = psi_off ? 0.0 : 0.5 * g * (orc_dpsi(0.0) - orc_dpsi(H / lam_w));
   double A1 = (2.0 - alpha) / alpha * (1.0 - 0.1817 * alpha);
   double A2 = 1.0 / PI + 0.5 * A1 * A1;
   double dx = 1.0;
@@ -340,14 +354,24 @@ double orc_tau_q(double lam_w, double mx_w, double alpha, double H) {
          dtt * dx * (12.0 + 30.0 * tt * vs * A1) / (16.0 * tt * tt);
 }
 
+double orc_tau_q(double lam_w, double mx_w, double alpha, double H) {
+  return tau_q_of(lam_w, mx_w, alpha, H, 0);
+}
+
 /* tilde tau_s(y) = lambda Psi(y) sqrt(6/(pi m_x)) for frozen lambda, m_x. */
 double orc_tau_s_tilde(double y, double H, double lam, double mx) {
   return lam * orc_Psi(y, H, lam) * sqrt(6.0 / (PI * mx));
 }
 
-/* r_sigma of Eq. R (first printed form) with c_m = c_m0 (2 - alpha)/alpha. */
-static double dbb_r(const orc_sim *S, double mx_w, double alpha) {
+/* r_sigma of Eq. R with c_m = c_m0 (2 - alpha)/alpha.  r_mode 0: the first
+ * printed form, the same for both species; 1: m_min replaced by m_sigma;
+ * 2: the second printed form with m_r = m_sigma / m_x (masses in units of
+ * m_min).  All three agree when m_a = m_b. */
+static double dbb_r(const orc_sim *S, double mx_w, double alpha, int sp) {
   double cm = S->p.c_m0 * (2.0 - alpha) / alpha;
+  if (S->p.r_mode == 1) return 2.0 - 2.0 / (1.0 + cm * sqrt(PI * mx_w / (6.0 * S->mh[sp])));
+  if (S->p.r_mode == 2)
+    return 2.0 - 2.0 / (1.0 + cm * sqrt(PI * mx_w / (6.0 * (S->mh[sp] / mx_w))));
   return 2.0 - 2.0 / (1.0 + cm / 3.0 * sqrt(PI * mx_w / (2.0 * S->kT)));
 }
 
@@ -377,7 +401,9 @@ orc_sim *orc_create(const orc_params *p) {
   if (!(p->m_a > 0 && p->m_b > 0 && p->C_l > 0 && p->C_l < 1 && p->theta >= 1 &&
         p->Kn_out > 0 && p->N >= 2 && p->N_x >= 4 && p->accommodation > 0 &&
         p->accommodation <= 1 && p->tau_rho > 0.5 && p->tau_e > 0.5 &&
-        p->tau_eps > 0.5 && p->mu_ratio_a > 0 && p->mu_ratio_b > 0))
+        p->tau_eps > 0.5 && p->mu_ratio_a > 0 && p->mu_ratio_b > 0 &&
+        (p->psi_off == 0 || p->psi_off == 1) && p->r_mode >= 0 && p->r_mode <= 2 &&
+        (p->lam_mode == 0 || p->lam_mode == 1)))
     return NULL;
   orc_sim *S = (orc_sim *)calloc(1, sizeof(orc_sim));
   S->p = *p;
@@ -481,10 +507,10 @@ static void collide_all(orc_sim *S) {
     node_state ns;
     get_node(S, S->f, x, 0, fa, fb);
     node_moments(S, fa, fb, 0, &ns);
-    tq_bot[x] = orc_tau_q(ns.lam, ns.mx, S->alpha[x], H);
+    tq_bot[x] = tau_q_of(ns.lam, ns.mx, S->alpha[x], H, S->p.psi_off);
     get_node(S, S->f, x, N - 1, fa, fb);
     node_moments(S, fa, fb, N - 1, &ns);
-    tq_top[x] = orc_tau_q(ns.lam, ns.mx, S->alpha[Nx + x], H);
+    tq_top[x] = tau_q_of(ns.lam, ns.mx, S->alpha[Nx + x], H, S->p.psi_off);
   }
 #pragma omp parallel for schedule(static)
   for (int x = 0; x < Nx; ++x) {
@@ -577,8 +603,8 @@ static void stream_and_bound(orc_sim *S) {
         n += r / S->mh[sp];
       }
       double alpha = S->alpha[wall * Nx + x];
-      double r_w = dbb_r(S, rho / n, alpha);
       for (int sp = 0; sp < 2; ++sp) {
+        double r_w = dbb_r(S, rho / n, alpha, sp);
         /* wall density with zero normal flux of this species:
          * sum_unknown f^eq_i(rho_w, u_w) = sum_outgoing f'_i */
         double out_sum = 0.0, eq_unit[Q], wsum = 0.0;
