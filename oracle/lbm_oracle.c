@@ -54,6 +54,7 @@
  * forms and independent special cases instead.
  */
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -107,6 +108,26 @@ typedef struct {
   int psi_off;
   int r_mode;
   int lam_mode;
+  /* Storage emulation (test mode, not part of the method): 0 none; else the
+   * post-collision populations of every updated node are kept as deviations
+   * from the rest equilibrium w_i alpha_si rhobar_s(x) of a per-column
+   * reference density (the initial profile) rounded to 1 FP32, 2 BF16,
+   * 3 FP16 after every collision; round to nearest, or stochastically when
+   * store_sr = 1 (round up with probability equal to the fraction of the
+   * spacing, from a counter-based generator seeded by store_seed).  Every
+   * reref_every steps (0 = never) the reference becomes the current column
+   * mean and the deviations are rounded again to nearest. */
+  int store_fmt;
+  int store_sr;
+  int reref_every;
+  unsigned store_seed;
+  /* Wall rule: 0 diffuse bounce-back (Eqs. bot, bot2); 1 bounce-back and
+   * specular reflection (BSR, the comparison scheme of the Method
+   * validation section): an unknown population takes the fraction r_b =
+   * 1/(1 + X) of its bounced-back partner at the node and 1 - r_b of its
+   * specularly reflected partner from the upstream neighbour, with X the
+   * factor of Eq. R (the DBB r is 2 - 2/(1 + X)). */
+  int wall;
 } orc_params;
 
 typedef struct {
@@ -121,6 +142,7 @@ typedef struct {
   int light;
   double Minv[Q][Q];
   double *alpha;   /* [2][Nx] accommodation, bottom then top */
+  double *refrho;  /* [2][Nx] reference densities of the storage emulation */
   double *f;       /* pre-collision state  [2][9][N][Nx] */
   double *fp;      /* post-collision state [2][9][N][Nx] */
   int have_post;   /* fp holds collide(f) (or a state set by the caller) */
@@ -363,16 +385,20 @@ double orc_tau_s_tilde(double y, double H, double lam, double mx) {
   return lam * orc_Psi(y, H, lam) * sqrt(6.0 / (PI * mx));
 }
 
-/* r_sigma of Eq. R with c_m = c_m0 (2 - alpha)/alpha.  r_mode 0: the first
- * printed form, the same for both species; 1: m_min replaced by m_sigma;
- * 2: the second printed form with m_r = m_sigma / m_x (masses in units of
- * m_min).  All three agree when m_a = m_b. */
-static double dbb_r(const orc_sim *S, double mx_w, double alpha, int sp) {
+/* The slip factor X of Eq. R, r_sigma = 2 - 2/(1 + X), with c_m = c_m0
+ * (2 - alpha)/alpha.  r_mode 0: the first printed form, the same for both
+ * species; 1: m_min replaced by m_sigma; 2: the second printed form with
+ * m_r = m_sigma / m_x (masses in units of m_min).  All three agree when
+ * m_a = m_b. */
+static double slip_X(const orc_sim *S, double mx_w, double alpha, int sp) {
   double cm = S->p.c_m0 * (2.0 - alpha) / alpha;
-  if (S->p.r_mode == 1) return 2.0 - 2.0 / (1.0 + cm * sqrt(PI * mx_w / (6.0 * S->mh[sp])));
-  if (S->p.r_mode == 2)
-    return 2.0 - 2.0 / (1.0 + cm * sqrt(PI * mx_w / (6.0 * (S->mh[sp] / mx_w))));
-  return 2.0 - 2.0 / (1.0 + cm / 3.0 * sqrt(PI * mx_w / (2.0 * S->kT)));
+  if (S->p.r_mode == 1) return cm * sqrt(PI * mx_w / (6.0 * S->mh[sp]));
+  if (S->p.r_mode == 2) return cm * sqrt(PI * mx_w / (6.0 * (S->mh[sp] / mx_w)));
+  return cm / 3.0 * sqrt(PI * mx_w / (2.0 * S->kT));
+}
+
+static double dbb_r(const orc_sim *S, double mx_w, double alpha, int sp) {
+  return 2.0 - 2.0 / (1.0 + slip_X(S, mx_w, alpha, sp));
 }
 
 double orc_dbb_r(double c_m0, double alpha, double mx_w) {
@@ -396,6 +422,85 @@ static int is_interior_col(const orc_sim *S, int x) {
   return S->p.x_periodic ? 1 : (x >= 1 && x <= S->Nx - 2);
 }
 
+/* ---------------------------------------------------------------------- */
+/* Storage emulation (test infrastructure for the error model of the      */
+/* reduced-precision storage; not part of the method).                    */
+/* ---------------------------------------------------------------------- */
+
+/* splitmix64 (Steele, Lea & Flood 2014) as a counter-based generator. */
+static uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+/* The two neighbours lo <= v < hi of v in a binary format with `digits`
+ * significant bits and smallest normal exponent emin (values below 2^emin
+ * have the spacing 2^(emin - digits + 1)); v is first rounded to FP32 as the
+ * kernel computes in FP32. */
+static double quantize(double v, int fmt, int stochastic, uint64_t counter) {
+  float v32 = (float)v;
+  if (fmt == 1 || v32 == 0.0f || !isfinite(v32)) return (double)v32;
+  const int digits = (fmt == 2) ? 8 : 11;
+  const int emin = (fmt == 2) ? -126 : -14;
+  int e;
+  frexp((double)v32, &e); /* v32 = m 2^e, 0.5 <= |m| < 1 */
+  int eu = e - digits;    /* spacing 2^eu */
+  if (e - 1 < emin) eu = emin - digits + 1;
+  const double ulp = ldexp(1.0, eu);
+  const double lo = floor((double)v32 / ulp) * ulp;
+  const double frac = ((double)v32 - lo) / ulp; /* in [0, 1) */
+  if (stochastic) {
+    double r = (double)(splitmix64(counter) >> 11) * (1.0 / 9007199254740992.0);
+    return r < frac ? lo + ulp : lo;
+  }
+  if (frac > 0.5) return lo + ulp;
+  if (frac < 0.5) return lo;
+  return fmod(lo / ulp, 2.0) == 0.0 ? lo : lo + ulp; /* ties to even */
+}
+
+static double cw_of(const orc_sim *S, int sp, int i) {
+  return i == 0 ? (9.0 - 5.0 * S->s[sp]) / 9.0 : (i < 5 ? S->s[sp] / 9.0 : S->s[sp] / 36.0);
+}
+
+/* Rounds the post-collision populations of the updated columns as stored
+ * deviations; then, on a re-referencing step, moves the reference to the
+ * column means and rounds again (to nearest). */
+static void emulate_storage(orc_sim *S) {
+  const int N = S->N, Nx = S->Nx, fmt = S->p.store_fmt;
+  const uint64_t step = (uint64_t)S->steps;
+  for (int sp = 0; sp < 2; ++sp)
+    for (int x = 0; x < Nx; ++x) {
+      if (!is_interior_col(S, x)) continue;
+      const double rb = S->refrho[sp * Nx + x];
+      for (int i = 0; i < Q; ++i)
+        for (int j = 0; j < N; ++j) {
+          size_t k = IDX(S, sp, i, j, x);
+          uint64_t ctr = ((uint64_t)S->p.store_seed << 40) ^ (step * 0x100000001B3ULL) ^ k;
+          double ref = cw_of(S, sp, i) * rb;
+          S->fp[k] = ref + quantize(S->fp[k] - ref, fmt, S->p.store_sr, ctr);
+        }
+    }
+  const long K = S->p.reref_every;
+  if (K <= 0 || (S->steps + 1) % K != 0) return;
+  for (int sp = 0; sp < 2; ++sp)
+    for (int x = 0; x < Nx; ++x) {
+      if (!is_interior_col(S, x)) continue;
+      double m = 0.0;
+      for (int j = 0; j < N; ++j)
+        for (int i = 0; i < Q; ++i) m += S->fp[IDX(S, sp, i, j, x)];
+      const double rb = m / N;
+      S->refrho[sp * Nx + x] = rb;
+      for (int i = 0; i < Q; ++i)
+        for (int j = 0; j < N; ++j) {
+          size_t k = IDX(S, sp, i, j, x);
+          double ref = cw_of(S, sp, i) * rb;
+          S->fp[k] = ref + quantize(S->fp[k] - ref, fmt, 0, 0);
+        }
+    }
+}
+
 orc_sim *orc_create(const orc_params *p) {
   if (!p) return NULL;
   if (!(p->m_a > 0 && p->m_b > 0 && p->C_l > 0 && p->C_l < 1 && p->theta >= 1 &&
@@ -403,7 +508,9 @@ orc_sim *orc_create(const orc_params *p) {
         p->accommodation <= 1 && p->tau_rho > 0.5 && p->tau_e > 0.5 &&
         p->tau_eps > 0.5 && p->mu_ratio_a > 0 && p->mu_ratio_b > 0 &&
         (p->psi_off == 0 || p->psi_off == 1) && p->r_mode >= 0 && p->r_mode <= 2 &&
-        (p->lam_mode == 0 || p->lam_mode == 1)))
+        (p->lam_mode == 0 || p->lam_mode == 1) && p->store_fmt >= 0 && p->store_fmt <= 3 &&
+        (p->store_sr == 0 || p->store_sr == 1) && p->reref_every >= 0 &&
+        (p->wall == 0 || p->wall == 1)))
     return NULL;
   orc_sim *S = (orc_sim *)calloc(1, sizeof(orc_sim));
   S->p = *p;
@@ -439,8 +546,9 @@ orc_sim *orc_create(const orc_params *p) {
   S->f = (double *)calloc(nn, sizeof(double));
   S->fp = (double *)calloc(nn, sizeof(double));
   S->alpha = (double *)malloc(sizeof(double) * 2 * S->Nx);
-  if (!S->f || !S->fp || !S->alpha) {
-    free(S->f); free(S->fp); free(S->alpha); free(S);
+  S->refrho = (double *)calloc(2 * (size_t)S->Nx, sizeof(double));
+  if (!S->f || !S->fp || !S->alpha || !S->refrho) {
+    free(S->f); free(S->fp); free(S->alpha); free(S->refrho); free(S);
     return NULL;
   }
   for (int k = 0; k < 2 * S->Nx; ++k) S->alpha[k] = p->accommodation;
@@ -449,7 +557,7 @@ orc_sim *orc_create(const orc_params *p) {
 
 void orc_destroy(orc_sim *S) {
   if (!S) return;
-  free(S->f); free(S->fp); free(S->alpha);
+  free(S->f); free(S->fp); free(S->alpha); free(S->refrho);
   free(S);
 }
 
@@ -474,6 +582,7 @@ void orc_init(orc_sim *S) {
     for (int sp = 0; sp < 2; ++sp) {
       double C = S->C_in[sp] + (S->C_out[sp] - S->C_in[sp]) * t;
       double rho_s = n * C * S->mh[sp];
+      S->refrho[sp * S->Nx + x] = rho_s;
       feq(rho_s, S->s[sp], 0.0, 0.0, fe);
       for (int j = 0; j < S->N; ++j)
         for (int i = 0; i < Q; ++i) S->f[IDX(S, sp, i, j, x)] = fe[i];
@@ -586,9 +695,48 @@ static void stream_and_bound(orc_sim *S) {
         }
   if (S->p.y_periodic) return;
   /* Diffuse bounce-back (Eqs. bot, bot2) at rows 1 and N, from the
-   * post-collision populations of the same node. */
+   * post-collision populations of the same node (or, with wall = 1, the
+   * bounce-back and specular-reflection rule). */
   static const int BOT_UNK[3] = {2, 5, 6}, TOP_UNK[3] = {4, 7, 8};
   static const int OPPQ[Q] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+  static const int SPECQ[Q] = {0, 1, 4, 3, 2, 8, 7, 6, 5}; /* mirror of c_y */
+  if (S->p.wall == 1) {
+    for (int wall = 0; wall < 2; ++wall) {
+      int j = wall == 0 ? 0 : N - 1;
+      const int *unk = wall == 0 ? BOT_UNK : TOP_UNK;
+      for (int x = 0; x < Nx; ++x) {
+        if (!is_interior_col(S, x)) continue;
+        double rho = 0.0, n = 0.0;
+        for (int sp = 0; sp < 2; ++sp) {
+          double r = col_density(S, P, sp, x, j);
+          rho += r;
+          n += r / S->mh[sp];
+        }
+        double alpha = S->alpha[wall * Nx + x];
+        for (int sp = 0; sp < 2; ++sp) {
+          double rb = 1.0 / (1.0 + slip_X(S, rho / n, alpha, sp));
+          for (int k = 0; k < 3; ++k) {
+            int i = unk[k], is = SPECQ[i];
+            /* the specular partner arrives from column x - c_ix */
+            int xs = x - CX[i];
+            double spec;
+            if (S->p.x_periodic) {
+              spec = P[IDX(S, sp, is, j, (xs + Nx) % Nx)];
+            } else if (xs == 0) {
+              spec = kin[sp] * (2.0 * P[IDX(S, sp, is, j, 1)] - P[IDX(S, sp, is, j, 2)]);
+            } else if (xs == Nx - 1) {
+              spec = kout[sp] *
+                     (2.0 * P[IDX(S, sp, is, j, Nx - 2)] - P[IDX(S, sp, is, j, Nx - 3)]);
+            } else {
+              spec = P[IDX(S, sp, is, j, xs)];
+            }
+            F[IDX(S, sp, i, j, x)] = rb * P[IDX(S, sp, OPPQ[i], j, x)] + (1.0 - rb) * spec;
+          }
+        }
+      }
+    }
+    return;
+  }
   for (int wall = 0; wall < 2; ++wall) {
     int j = wall == 0 ? 0 : N - 1;
     const int *unk = wall == 0 ? BOT_UNK : TOP_UNK;
@@ -623,9 +771,15 @@ static void stream_and_bound(orc_sim *S) {
   }
 }
 
+/* Collision of the current state into fp (and its storage emulation). */
+static void collide_now(orc_sim *S) {
+  collide_all(S);
+  if (S->p.store_fmt) emulate_storage(S);
+}
+
 void orc_step(orc_sim *S, long nsteps) {
   for (long t = 0; t < nsteps; ++t) {
-    if (!S->have_post) collide_all(S);
+    if (!S->have_post) collide_now(S);
     stream_and_bound(S);
     S->have_post = 0;
     S->post_only = 0;
@@ -636,7 +790,7 @@ void orc_step(orc_sim *S, long nsteps) {
 /* Post-collision state of the current step, canonical layout. */
 void orc_get_post_state(orc_sim *S, double *out) {
   if (!S->have_post) {
-    collide_all(S);
+    collide_now(S);
     S->have_post = 1;
   }
   memcpy(out, S->fp, sizeof(double) * 2 * Q * S->N * S->Nx);
@@ -756,7 +910,7 @@ void orc_separation(orc_sim *S, double *CL, double *Cl_tilde, double *mdot_a,
  * post-collision state (ghost columns included). */
 void orc_face_flux(orc_sim *S, double *Fa, double *Fb) {
   const int N = S->N, Nx = S->Nx;
-  if (!S->have_post) { collide_all(S); S->have_post = 1; }
+  if (!S->have_post) { collide_now(S); S->have_post = 1; }
   const double *P = S->fp;
   double kin[2] = {1, 1}, kout[2] = {1, 1};
   if (!S->p.x_periodic)

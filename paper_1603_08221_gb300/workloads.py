@@ -11,7 +11,10 @@ from __future__ import annotations
 
 import numpy as np
 
-# Molecular masses (g/mol) of the paper's two mixtures (Sec. 2).
+# Molecular masses (g/mol, standard atomic weights) of helium, neon and argon.
+# The paper states only the mass ratios of its two mixtures, 1:10 for He-Ar
+# and 1:2 for Ne-Ar (Sec. 2); these are the masses of the benchmark
+# configurations, whose ratios round to those.
 HE, NE, AR = 4.003, 20.18, 39.948
 
 #: Named problems. Each is a dict of the physical inputs of Sec. 2 (masses,

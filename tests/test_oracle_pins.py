@@ -145,6 +145,57 @@ def test_mid_step_species_momentum(orc, seed):
         assert np.allclose(0.5 * (j + jp), eq_rhou, rtol=1e-13, atol=1e-15)
 
 
+@pytest.mark.parametrize("masses", [(workloads.HE, workloads.AR), (workloads.AR, workloads.NE)])
+def test_moments_and_separation_of_a_given_state_unequal_masses(orc, masses):
+    """orc_moments and orc_separation on a random state of two gases of
+    unequal mass (the light one first, then second):
+      - rho_s u_s of Eq. rhou is the mean of the species momenta before and
+        after one collision with the node's own tau_d (j'_s from the
+        Gauss-Jordan collision, not from the weights of Eq. rhou);
+      - C_l(x) of Eq. C is the column's light-species number fraction
+        sum_j n_l / sum_j (n_a + n_b), n_s = rho_s / m_s, from the raw
+        populations (a mass fraction would differ by the 1:10 or 1:2 mass
+        ratio);
+      - CL of Eq. CL uses the imposed inlet fraction; mdot_s is the mean
+        over the updated columns of sum_j rho_s u_s,x."""
+    m_a, m_b = masses
+    N, Nx = 5, 9
+    o = orc.Oracle(dict(m_a=m_a, m_b=m_b, C_l=0.4, theta=2.0, Kn_out=0.2, N=N, N_x=Nx))
+    f = workloads.random_post_state(N, Nx, seed=21)
+    o.set_post_state(f)
+    mom = o.moments()
+    sep = o.separation()
+    light = 0 if m_a < m_b else 1
+    mass = (m_a, m_b)
+    jbar = np.zeros((2, N, Nx))
+    for x in range(1, Nx - 1):
+        for j in range(N):
+            fa, fb = f[0, :, j, x], f[1, :, j, x]
+            t = o.node_taus(fa, fb, j)
+            tau = np.array([1.0, 1.1, 1.2, t["tau_d"], 1.3, t["tau_d"], 1.3, t["tau_s"],
+                            t["tau_s"]])
+            oa, ob = o.collide_node(fa, fb, tau)
+            for sp, (pre, post) in enumerate(((fa, oa), (fb, ob))):
+                jx = 0.5 * ((CX * pre).sum() + (CX * post).sum())
+                jy = 0.5 * ((CY * pre).sum() + (CY * post).sum())
+                rho = pre.sum()
+                key = "ua" if sp == 0 else "ub"
+                assert abs(mom[key + "_x"][j, x] * rho - jx) < 1e-13 * rho
+                assert abs(mom[key + "_y"][j, x] * rho - jy) < 1e-13 * rho
+                jbar[sp, j, x] = jx
+    n = f.sum(axis=1) / np.array(mass)[:, None, None]  # number densities [2][N][Nx]
+    C = n[light].sum(axis=0) / n.sum(axis=(0, 1))
+    inner = slice(1, Nx - 1)
+    assert np.allclose(sep["Cl_profile"][inner], C[inner], rtol=1e-14, atol=0)
+    assert sep["Cl_profile"][0] == 0.4 and sep["Cl_profile"][-1] == 0.4
+    xm = 1 + int(np.argmin(C[inner]))
+    assert sep["x_min"] == xm
+    assert abs(sep["CL"] - (0.4 - C[xm]) / 0.4) < 1e-14
+    for sp, key in ((0, "mdot_a"), (1, "mdot_b")):
+        expect = jbar[sp][:, inner].sum(axis=0).mean()
+        assert abs(sep[key] - expect) < 1e-13 * abs(expect)
+
+
 @pytest.mark.parametrize("tau", [0.7, 1.0, 1.9])
 def test_bgk_limit(orc, tau):
     """P12: with all relaxation times equal, the MRT collision is the BGK

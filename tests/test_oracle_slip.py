@@ -36,14 +36,19 @@ def _moment_basis():
     return np.array(rows, dtype=float)
 
 
-def _x_invariant_channel(N, tau_s, tau_q, r, G, tau_e, tau_eps, tau_d):
+SPEC = [0, 1, 4, 3, 2, 8, 7, 6, 5]  # mirror image of c_y
+
+
+def _x_invariant_channel(N, tau_s, tau_q, r, G, tau_e, tau_eps, tau_d, wall="dbb"):
     """Exact steady state of the linearised single-gas D2Q9 MRT channel with
-    DBB walls (Eqs. MRT, MR, bot, bot2) driven by a uniform pressure gradient
+    DBB walls (Eqs. MRT, MR, bot, bot2; wall="bsr": bounce-back fraction r,
+    specular reflection 1 - r) driven by a uniform pressure gradient
     G = -dp/dx, solved as one linear system.  Around the rest state the
     x-dependent part w_i rho(x) of a pressure-driven solution streams into
     w_i rho(x) + 3 w_i c_ix G, so the x-invariant remainder sees that source
-    at every streaming step (not at the wall rule, which maps w_i rho(x) to
-    itself).  Returns u_x (= j_x, rest density 1) per row."""
+    at every streaming step and at every specular reflection, which also
+    moves the population by c_ix (not at the same-node rules, which map
+    w_i rho(x) to itself).  Returns u_x (= j_x, rest density 1) per row."""
     M = _moment_basis()
     Minv = np.linalg.inv(M)
     S = np.diag([1, 1 / tau_e, 1 / tau_eps, 1 / tau_d, 1 / tau_q, 1 / tau_d, 1 / tau_q,
@@ -61,54 +66,63 @@ def _x_invariant_channel(N, tau_s, tau_q, r, G, tau_e, tau_eps, tau_d):
             if 0 <= js < N:
                 A[row, 9 * js:9 * js + 9] -= C[i]
                 b[row] = 3 * W[i] * CX[i] * G
-            else:  # r f^eq(rho_w, u_w = 0) + (1 - r) f'_opp of the same node
+            elif wall == "dbb":  # r f^eq(rho_w, u_w = 0) + (1 - r) f'_opp, same node
                 o = OPP[i]
                 outgoing = [k for k in range(9) if CY[k] == CY[o]]
                 for k in outgoing:
                     A[row, 9 * j:9 * j + 9] -= r * W[i] * 6 * C[k]
                 A[row, 9 * j:9 * j + 9] -= (1 - r) * C[o]
+            else:  # r f'_opp of the node + (1 - r) f'_spec of the upstream node
+                A[row, 9 * j:9 * j + 9] -= r * C[OPP[i]] + (1 - r) * C[SPEC[i]]
+                b[row] = (1 - r) * 3 * W[i] * CX[i] * G
     A[-1, :] = 1.0  # the mass is free: fix it
     b[-1] = N
     f = np.linalg.solve(A, b).reshape(N, 9)
     return f @ CX
 
 
-def _discrete_slip(N, tau_s, tau_q, r, G):
+def _discrete_slip(N, tau_s, tau_q, r, G, wall="dbb"):
     """Closed form of the exact discrete steady profile: parabolic with
     curvature G/(2 nu), nu = (tau_s - 1/2)/3, and wall value
     a = (G/nu) [H t q/2 + (16 Lambda - 3)/24 - t q/6], t = tau_s - 1/2,
-    Lambda = t (tau_q - 1/2), q = r/(2 - r), H = N."""
+    Lambda = t (tau_q - 1/2), q = r/(2 - r), H = N (DBB), or
+    a = (G/nu) [H t q/2 + (16 Lambda - 3)/24], q = (1 - r)/r (BSR)."""
     t = tau_s - 0.5
     nu = t / 3
-    q = r / (2 - r)
+    q = r / (2 - r) if wall == "dbb" else (1 - r) / r
     lam = t * (tau_q - 0.5)
     y = np.arange(N) + 0.5
-    a = G / nu * (N * t * q / 2 + (16 * lam - 3) / 24 - t * q / 6)
+    rem = t * q / 6 if wall == "dbb" else 0.0
+    a = G / nu * (N * t * q / 2 + (16 * lam - 3) / 24 - rem)
     return a + G / (2 * nu) * y * (N - y)
 
 
-def test_discrete_slip_closed_form_against_direct_solve():
-    """Brute force on small channels: for random relaxation times, DBB
+@pytest.mark.parametrize("wall", ["dbb", "bsr"])
+def test_discrete_slip_closed_form_against_direct_solve(wall):
+    """Brute force on small channels: for random relaxation times, wall
     parameters and widths the direct solve equals the closed form to
-    round-off.  tau_e, tau_eps, tau_d do not enter.  With
+    round-off.  tau_e, tau_eps, tau_d do not enter.  DBB: with
     r/(2 - r) = varsigma c_m (Eq. R) the first term is the first-order slip
     c_m lambda du/dn (lambda = varsigma t, Eq. EQFrb); with tau_q of Eq. taoq
     at uniform tau_s the middle term is A_2 lambda^2 G/nu (the second-order
-    slip) and the last, -varsigma c_m G/2, is the remainder."""
+    slip) and the last, -varsigma c_m G/2, is a remainder.  BSR with
+    (1 - r)/r = varsigma c_m realises both terms with no remainder: Eq.
+    taoq is exact for it."""
     rng = np.random.default_rng(7)
     G = 1e-3
     for _ in range(12):
         N = int(rng.integers(4, 14))
         ts, tq = 0.55 + rng.uniform(0, 4, size=2)
-        r = rng.uniform(0.0, 1.9)
-        u = _x_invariant_channel(N, ts, tq, r, G, *rng.uniform(0.6, 2.0, size=3))
-        ref = _discrete_slip(N, ts, tq, r, G)
+        r = rng.uniform(0.0, 1.9) if wall == "dbb" else rng.uniform(0.05, 1.0)
+        u = _x_invariant_channel(N, ts, tq, r, G, *rng.uniform(0.6, 2.0, size=3), wall=wall)
+        ref = _discrete_slip(N, ts, tq, r, G, wall=wall)
         assert np.abs(u - ref).max() < 1e-10 * np.abs(ref).max()
 
 
-def _steady(orc, N, Kn, alpha, c_m0, psi_off, L_over_H=6.0, theta=1.001, tol=1e-12):
+def _steady(orc, N, Kn, alpha, c_m0, psi_off, L_over_H=6.0, theta=1.001, tol=1e-12,
+            wall_mode=0):
     p = dict(m_a=2.0, m_b=2.0, C_l=0.4, theta=theta, Kn_out=Kn, N=N, L_over_H=L_over_H,
-             accommodation=alpha, c_m0=c_m0, psi_off=psi_off)
+             accommodation=alpha, c_m0=c_m0, psi_off=psi_off, wall=wall_mode)
     o = orc.Oracle(p)
     o.init()
     prev = None
@@ -157,6 +171,26 @@ def test_single_gas_poiseuille_slip_uniform_mfp(orc, N, Kn, alpha, c_m0):
     y = np.arange(N) + 0.5
     u_s = c_m * lam * G * H / (2 * mu) + A2 * lam**2 * G / mu - VS * c_m * G / (2 * rho)
     ref = G / (2 * mu) * y * (H - y) + u_s
+    assert G > 0
+    assert np.abs(u - ref).max() < 1e-5 * ref.max()
+
+
+@pytest.mark.parametrize("N,Kn,alpha,c_m0", [
+    (8, 0.05, 1.0, 1 - 0.1817),
+    (16, 0.3, 0.8, 1 - 0.1817 * 0.8),
+    (12, 0.1, 0.6, 1.016),
+])
+def test_single_gas_poiseuille_slip_bsr_wall(orc, N, Kn, alpha, c_m0):
+    """The bounce-back / specular-reflection wall (the comparison scheme of
+    the Method validation section) with bounce-back fraction 1/(1 + X), X
+    the factor of Eq. R, and tau_q of Eq. taoq realises the second-order slip
+    solution exactly (measured to 3e-7, the pressure ratio's nonlinearity):
+        G/(2 mu) y (H - y) + c_m lambda G H/(2 mu) + A_2 lambda^2 G/mu."""
+    u, G, lam, mu, rho = _steady(orc, N, Kn, alpha, c_m0, psi_off=1, wall_mode=1)
+    A1, A2 = _A(alpha)
+    c_m = c_m0 * (2 - alpha) / alpha
+    y = np.arange(N) + 0.5
+    ref = G / (2 * mu) * y * (N - y) + c_m * lam * G * N / (2 * mu) + A2 * lam**2 * G / mu
     assert G > 0
     assert np.abs(u - ref).max() < 1e-5 * ref.max()
 
