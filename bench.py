@@ -136,9 +136,11 @@ def kernel_source_sha256():
     return hashlib.sha256(text[:end]).hexdigest()
 
 
-def oracle_throughput(steps: int, sample: str, threads: int = 0):
+def oracle_throughput(steps: int, sample: str, threads: int = 0, keep: bool = False):
     """FP64 oracle MLUPS on the host cores over `steps` steps of `sample`
-    (threads >= 1: on that many OpenMP threads)."""
+    (threads >= 1: on that many OpenMP threads).  The timed steps follow one
+    untimed step, so the oracle ends at step steps + 1; keep=True also
+    returns it."""
     import oracle
     from paper_1603_08221_gb300 import workloads
 
@@ -155,17 +157,47 @@ def oracle_throughput(steps: int, sample: str, threads: int = 0):
     finally:
         oracle.set_num_threads(0)
     nodes = o.N * (o.N_x - 2)
-    return nodes * steps / dt / 1e6, dt, used, nodes
+    out = (nodes * steps / dt / 1e6, dt, used, nodes)
+    return out + (o,) if keep else out
+
+
+def parity_against_oracle(o, stream):
+    """Errors of the GPU FP32 path against the FP64 oracle object `o` after
+    the same number of steps on the same channel: max |error| over the field
+    relative to the field's max for rho_s, u_s (x and y, scaled by the
+    largest |u_x|), and the scalar diagnostics."""
+    import numpy as np
+    from paper_1603_08221_gb300 import binding
+    g = binding.LbmMix(stream=stream, **o.params_dict)
+    g.init()
+    g.step(o.steps)
+    mg, mo = g.moments(), o.moments()
+    sg, so = g.separation(), o.separation()
+    g.close()
+    uscale = max(np.abs(mo["ua_x"]).max(), np.abs(mo["ub_x"]).max())
+    err = {"steps": o.steps,
+           "rho_rel": max(float(np.abs(mg[k] - mo[k]).max() / np.abs(mo[k]).max())
+                          for k in ("rho_a", "rho_b")),
+           "u_rel": max(float(np.abs(mg[k] - mo[k]).max() / uscale)
+                        for k in ("ua_x", "ua_y", "ub_x", "ub_y")),
+           "CL": so["CL"], "CL_abs": abs(sg["CL"] - so["CL"]),
+           "mdot_rel": max(abs(sg[k] - so[k]) / abs(so[k]) for k in ("mdot_a", "mdot_b")),
+           "Cl_profile_abs": float(np.abs(sg["Cl_profile"] - so["Cl_profile"]).max())}
+    return err
 
 
 def run_sweep(args, rank, world, barrier):
-    """The seeded 96-channel parametric study run to a residual of 1e-8 (or
-    the step cap): once as a graph-replayed concurrent sweep with the
-    schedule autotuner, once as sequential lone runs (plain launches).
-    Instances are dealt round-robin over the ranks."""
+    """The seeded 96-channel parametric study, every instance run to a
+    steady-state residual of 1e-8 (or the step cap, or divergence), as one
+    graph-replayed concurrent sweep with the schedule autotuner.  The
+    sequential baseline (lone handles, plain launches, the same convergence
+    test) is timed on every fourth instance and scaled to the whole study by
+    node updates (each lone run takes exactly its instance's steps in the
+    sweep).  Instances are dealt round-robin over the ranks."""
     from paper_1603_08221_gb300 import binding, workloads
     inst = workloads.sweep_instances()
-    mine = [p for k, p in enumerate(inst) if k % world == rank]
+    ids = [k for k in range(len(inst)) if k % world == rank]
+    mine = [inst[k] for k in ids]
     tol, check = 1e-8, 1000
     sw = binding.LbmSweep(mine)
     sw.init()
@@ -176,9 +208,11 @@ def run_sweep(args, rank, world, barrier):
     t_sweep = time.perf_counter() - t0
     policy, _, round_ms = sw.schedule()
     sw.close()
+    upd = [p["N"] * (workloads.n_x(p) - 2) * n for p, n in zip(mine, steps)]
+    sub = [i for i, k in enumerate(ids) if k % args.sweep_seq_every == 0]
     t0 = time.perf_counter()
-    for k, p in enumerate(mine):
-        g = binding.LbmMix(**p)
+    for i in sub:
+        g = binding.LbmMix(**mine[i])
         g.init()
         try:
             g.run_to_steady(tol, args.sweep_cap, check)
@@ -187,26 +221,41 @@ def run_sweep(args, rank, world, barrier):
                 raise
         g.close()
     barrier()
-    t_seq = time.perf_counter() - t0
-    solved = sum(1 for st in status if st == binding.LBM_OK)
-    updates = sum(p["N"] * (workloads.n_x(p) - 2) * n for p, n in zip(mine, steps))
+    t_sub = time.perf_counter() - t0
+    upd_sub = sum(upd[i] for i in sub)
+    conv = [k for k, st in zip(ids, status) if st == binding.LBM_OK]
+    capped = [k for k, st in zip(ids, status) if st == binding.LBM_ENOTCONVERGED]
+    div = [k for k, st in zip(ids, status) if st == binding.LBM_ENONFINITE]
+    updates = sum(upd)
+    t_seq = t_sub * updates / max(upd_sub, 1)
     if world > 1:
         import torch
         import torch.distributed as dist
-        t = torch.tensor([t_sweep, t_seq], dtype=torch.float64, device="cuda")
+        t = torch.tensor([t_sweep, t_seq, t_sub], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        c = torch.tensor([solved, updates], dtype=torch.float64, device="cuda")
+        c = torch.tensor([updates], dtype=torch.float64, device="cuda")
         dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        t_sweep, t_seq = float(t[0]), float(t[1])
-        solved, updates = int(c[0]), int(c[1])
+        t_sweep, t_seq, t_sub = float(t[0]), float(t[1]), float(t[2])
+        updates = int(c[0])
+        lists = [None] * world
+        dist.all_gather_object(lists, (conv, capped, div))
+        conv = sorted(k for l in lists for k in l[0])
+        capped = sorted(k for l in lists for k in l[1])
+        div = sorted(k for l in lists for k in l[2])
     return {"instances": len(inst), "tol": tol, "check_every": check,
-            "step_cap": args.sweep_cap, "solves": solved, "seconds": t_sweep,
-            "solves_per_s": solved / t_sweep, "sequential_seconds": t_seq,
-            "sequential_solves_per_s": solved / t_seq, "speedup": t_seq / t_sweep,
+            "step_cap": args.sweep_cap, "solves": len(conv), "seconds": t_sweep,
+            "solves_per_s": len(conv) / t_sweep,
+            "sequential_seconds": t_seq,
+            "sequential_solves_per_s": len(conv) / t_seq, "speedup": t_seq / t_sweep,
+            "sequential_sample": f"every {args.sweep_seq_every}th instance timed as lone runs "
+                                 f"({t_sub:.1f} s), scaled by node updates",
             "aggregate_mlups": updates / t_sweep / 1e6,
-            "outcomes": {"converged": status.count(binding.LBM_OK),
-                         "step_cap": status.count(binding.LBM_ENOTCONVERGED),
-                         "diverged": status.count(binding.LBM_ENONFINITE)},
+            "outcomes": {"converged": len(conv), "step_cap": len(capped),
+                         "diverged": len(div)},
+            "diverged_instances": [dict(index=k, theta=round(inst[k]["theta"], 3),
+                                        Kn_out=round(inst[k]["Kn_out"], 4), N=inst[k]["N"])
+                                   for k in div],
+            "capped_instances": capped,
             "autotuned_policy": policy, "autotune_block_ms": round_ms}
 
 
@@ -295,12 +344,14 @@ def run_ours(args):
 
     from paper_1603_08221_gb300 import binding, workloads
     binding.load()
+    storage = {"fp32": binding.LBM_FP32, "bf16": binding.LBM_BF16,
+               "fp16": binding.LBM_FP16}[args.storage]
     p = workloads.preset(args.workload, diag_every=args.diag_every)
     # a dedicated (non-default) stream: the library and the CUDA events below
     # must see the same stream
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    sim = binding.LbmMix(stream=stream, **p)
+    sim = binding.LbmMix(stream=stream, storage=storage, **p)
     nodes = sim.N * (sim.N_x - 2)
     sim.init()
 
@@ -381,28 +432,34 @@ def run_ours(args):
     if rank != 0:
         return 0
     peak, peak_kind = measured_peak_hbm()
-    achieved = BYTES_PER_NODE * nodes / (elapsed / args.steps) / 1e9
-    traffic = profiled_traffic()
+    bytes_per_node = BYTES_PER_NODE if args.storage == "fp32" else BYTES_PER_NODE // 2
+    achieved = bytes_per_node * nodes / (elapsed / args.steps) / 1e9
+    traffic = profiled_traffic() if args.storage == "fp32" else None
     cpu = None
+    parity = None
     if world == 1 and not args.no_cpu_baseline:
-        c_mlups, c_dt, cores, c_nodes = oracle_throughput(args.cpu_steps, REF_SAMPLE)
-        s_steps = max(1, args.cpu_steps // 10)
+        c_mlups, c_dt, cores, c_nodes, o = oracle_throughput(args.cpu_steps - 1, REF_SAMPLE,
+                                                             keep=True)
+        s_steps = max(1, args.cpu_steps // 20)
         s_mlups, s_dt, _, _ = oracle_throughput(s_steps, REF_SAMPLE, threads=1)
         cpu = {"value": c_mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": f"FP64 oracle, {args.cpu_steps} steps of the {REF_SAMPLE} 1/16 "
                          f"linear-scale copy ({c_nodes} nodes, {c_dt:.1f} s)",
                "single_thread": {"value": s_mlups, "unit": "MLUPS", "cores": 1,
                                  "sample": f"{s_steps} steps of the same copy ({s_dt:.1f} s)"}}
+        o.params_dict = workloads.preset(REF_SAMPLE)
+        parity = dict(workload=REF_SAMPLE, **parity_against_oracle(o, stream))
     line = {
         "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
         "value_per_species_set": 2 * mlups,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.storage == "fp32" else f"f32 compute, {args.storage} storage",
         "data": "synthetic",
         "config": {"workload": args.workload, "N": sim.N, "N_x": sim.N_x,
                    "m_a": p["m_a"], "m_b": p["m_b"], "C_l": p["C_l"], "theta": p["theta"],
                    "Kn_out": p["Kn_out"], "nodes_updated": nodes,
-                   "bytes_per_node_step": BYTES_PER_NODE,
+                   "bytes_per_node_step": bytes_per_node, "storage": args.storage,
                    "diag_every": args.diag_every,
                    "l2": "state (2 x 1.2 GB FP32) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
@@ -412,6 +469,7 @@ def run_ours(args):
                      "nominal_peak": NOMINAL_HBM_GBS,
                      "frac_of_nominal": achieved / NOMINAL_HBM_GBS},
         "cpu_baseline": cpu,
+        "parity_vs_oracle": parity,
         "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h / args.steps},
         "gpu_launches": args.steps,
@@ -435,7 +493,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--cpu-steps", type=int, default=1000)
+    ap.add_argument("--storage", choices=["fp32", "bf16", "fp16"], default="fp32",
+                    help="population storage of the timed channel (FP32 is the headline)")
+    ap.add_argument("--cpu-steps", type=int, default=2000,
+                    help="oracle steps of the 1/16 copy: the CPU baseline and the parity check")
     ap.add_argument("--diag-every", type=int, default=100,
                     help="steps between FP64 separation-diagnostic reductions (the column "
                          "sums of the end columns are reduced every step)")
@@ -448,8 +509,11 @@ def main():
                     help="steps of the adjoint workload (5000 for the sensitivity study)")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the 96-channel parametric sweep")
-    ap.add_argument("--sweep-cap", type=int, default=10000,
-                    help="step cap per sweep instance (200000 for the full study)")
+    ap.add_argument("--sweep-cap", type=int, default=200000,
+                    help="step cap per sweep instance")
+    ap.add_argument("--sweep-seq-every", type=int, default=4,
+                    help="time every n-th sweep instance as a lone run for the sequential "
+                         "baseline")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -48,6 +48,25 @@ extern "C" {
 #define LBM_BF16 1 /* BF16 deviations (72 B per node per step) */
 #define LBM_FP16 2 /* FP16 deviations (72 B per node per step) */
 
+/* Rounding of the BF16/FP16 stores of the step.  Round to nearest repeats
+ * the same rounding error every step once the flow is steady, and the
+ * collision conserves the momentum that error carries, so it accumulates
+ * into a bias of the velocity field; stochastic rounding makes each
+ * rounding error zero-mean and independent of the previous step's. */
+#define LBM_ROUND_STOCHASTIC 0 /* default: stochastic rounding (hardware cvt.rs) */
+#define LBM_ROUND_NEAREST 1    /* round to nearest even */
+
+/* Wall rule.  The paper's diffuse bounce-back (Eqs. bot, bot2) with r of
+ * Eq. R, or the bounce-back and specular-reflection scheme it validates
+ * against (Method validation section): an unknown population is the
+ * fraction r_b = 1/(1 + X) of its bounced-back partner at the node plus
+ * 1 - r_b of its specularly reflected partner from the upstream neighbour
+ * column, X the slip factor of Eq. R (r = 2 - 2/(1 + X)); both give the
+ * first-order slip c_m lambda du/dn, and with tau_q of Eq. taoq the BSR
+ * scheme also gives the second-order term of Eq. A12 exactly. */
+#define LBM_WALL_DBB 0 /* default */
+#define LBM_WALL_BSR 1
+
 typedef struct lbm_mix lbm_mix; /* opaque, owned by the library */
 
 /* Physical problem (Sec. 2, Table 1) and model knobs (Sec. 3). */
@@ -71,12 +90,16 @@ typedef struct {
   int reref_every;      /* steps between re-referencings of the stored deviations
                            (lbm_mix_rereference); 0 = never; -1 = 256 for BF16/FP16
                            storage and never for FP32 */
+  int rounding;         /* BF16/FP16 stores: LBM_ROUND_STOCHASTIC or LBM_ROUND_NEAREST
+                           (FP32 storage ignores it) */
+  int wall;             /* LBM_WALL_DBB or LBM_WALL_BSR */
 } lbm_mix_params;
 
 /* Fills the defaults: He-Ar (4.003, 39.948), C_l = 0.5, C_l_out = -1,
  * theta = 2, Kn_out = 0.1, N = 16, N_x = 0, L_over_H = 20, alpha = 1,
  * c_m0 = 1.016, tau_rho = 1, tau_e = 1.1, tau_eps = 1.2, mu ratios 1,
- * LBM_FP32, x_periodic = 0, diag_every = 1, reref_every = -1.  NULL-safe. */
+ * LBM_FP32, x_periodic = 0, diag_every = 1, reref_every = -1,
+ * rounding = LBM_ROUND_STOCHASTIC, wall = LBM_WALL_DBB.  NULL-safe. */
 void lbm_mix_default_params(lbm_mix_params* p);
 
 /* Validates p, derives the lattice constants (Eqs. P, EQFrb, rho2 with the
@@ -251,6 +274,9 @@ int lbm_mix_eval_special(const double* x, double* e1, double* psi, long n);
  *   d_cl_profile  N_x doubles written: C_l(x) of the new state.
  * The first call on a device looks up the static array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The address is looked up again when the calling thread's current context
+ * is not the one of the last lookup (after cudaDeviceReset, for example),
+ * so the first call after a reset must also come before any capture.
  * Every call shares the one array and resets its counters, so calls whose
  * kernels overlap on the GPU (different streams, or different threads
  * without ordering) race and corrupt each other's results; serialise them.
@@ -306,6 +332,11 @@ int lbm_sweep_step(lbm_sweep* s, long nsteps);
  * boundaries, so the same step counts as a lone run) until its residual
  * drops to tol (status LBM_OK), it has taken max_steps (LBM_ENOTCONVERGED)
  * or turns non-finite (LBM_ENONFINITE); converged instances stop stepping.
+ * A graph is replayed only while the instance's buffer parity, schedule,
+ * reference-density table and step phase are those it was captured from;
+ * calls on a borrowed handle that change them (odd step counts, state
+ * uploads, lbm_mix_set_rows_per_block, lbm_mix_rereference) lead to a new
+ * capture.
  * autotune != 0: the first LBM_SWEEP_NPOLICY blocks run under each
  * node-to-CTA schedule in turn (real steps, timed on the host around the
  * whole block), the rest under the fastest.  steps_out, residual_out,
@@ -349,8 +380,9 @@ typedef struct lbm_adj lbm_adj;
 #define LBM_ADJ_FLUX 1
 
 /* Validates p like lbm_mix_create (storage is ignored: FP64; x_periodic
- * channels are rejected: the adjoint covers the pressure-driven channel with
- * its inlet and outlet, Eqs. rho1 and rho2) and allocates
+ * channels and the BSR wall are rejected: the adjoint covers the
+ * pressure-driven channel with its inlet and outlet, Eqs. rho1 and rho2,
+ * between DBB walls) and allocates
  * the checkpoints (ceil(nsteps/checkpoint_every) + 1 states of 18 N N_x
  * doubles) and one interval of replayed states.  stream: cudaStream_t or
  * NULL for an own stream.  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */

@@ -27,6 +27,10 @@ LBM_ETIMEOUT = -6
 LBM_FP32 = 0
 LBM_BF16 = 1
 LBM_FP16 = 2
+LBM_ROUND_STOCHASTIC = 0
+LBM_ROUND_NEAREST = 1
+LBM_WALL_DBB = 0
+LBM_WALL_BSR = 1
 
 
 class lbm_mix_params(ctypes.Structure):
@@ -43,6 +47,8 @@ class lbm_mix_params(ctypes.Structure):
         ("storage", ctypes.c_int), ("x_periodic", ctypes.c_int),
         ("diag_every", ctypes.c_int),
         ("reref_every", ctypes.c_int),
+        ("rounding", ctypes.c_int),
+        ("wall", ctypes.c_int),
     ]
 
 

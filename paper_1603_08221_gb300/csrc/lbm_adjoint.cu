@@ -995,6 +995,8 @@ int lbm_adj_create(const lbm_mix_params* p, long nsteps, int checkpoint_every, v
     return lbm_internal_error(LBM_EINVAL, "need nsteps >= 1 and checkpoint_every >= 1");
   if (p->x_periodic)
     return lbm_internal_error(LBM_EINVAL, "the adjoint covers channels with pressure ends only");
+  if (p->wall != LBM_WALL_DBB)
+    return lbm_internal_error(LBM_EINVAL, "the adjoint covers the diffuse bounce-back wall only");
   lbm_adj* a = new (std::nothrow) lbm_adj;
   if (!a) return lbm_internal_error(LBM_ENOMEM, "host allocation failed");
   a->p = *p;
@@ -1144,6 +1146,10 @@ int lbm_adj_gradient(lbm_adj* a, int objective, double* dtheta, double* dkn, dou
   CKA(cudaGetLastError());
   int cur = 0;  // lam[cur] is the adjoint of the state after the step being reversed
   const long nseg = (a->T + a->K - 1) / a->K;
+  // the replay's last output of a segment is not needed (only its column
+  // data are); it goes to the work buffer that does not hold f^T, so that
+  // lbm_adj_state still returns the forward run's final state afterwards
+  double* spare = a->work[1 - (a->T & 1)];
   for (long sg = nseg - 1; sg >= 0; --sg) {
     const long t0 = sg * a->K;  // segment replays steps t0+1 .. t1
     const long t1 = (t0 + a->K < a->T) ? t0 + a->K : a->T;
@@ -1153,7 +1159,7 @@ int lbm_adj_gradient(lbm_adj* a, int objective, double* dtheta, double* dkn, dou
     for (long t = t0 + 1; t <= t1; ++t) {
       const long k = t - t0 - 1;
       double* fin = a->seg + a->S * (size_t)k;
-      double* fo = (t < t1) ? a->seg + a->S * (size_t)(k + 1) : a->work[0];
+      double* fo = (t < t1) ? a->seg + a->S * (size_t)(k + 1) : spare;
       int st = fwd_step(a, fin, fo, cols_of(a, a->segcols + cw * k));
       if (st) return st;
     }

@@ -75,6 +75,7 @@ struct Lat {
   int N, Nx, pitch;
   unsigned SS;           // floats per strip: N * RS
   int x_periodic;
+  int wall_mode;         // LBM_WALL_DBB or LBM_WALL_BSR
   int light;             // index of the light species
   float s[2];            // s_sigma = m_min / m_sigma
   float cw0[2];          // rest-equilibrium weights w_i alpha_si: rest (9 - 5s)/9,
@@ -262,9 +263,25 @@ struct Stor<float> {
   static __device__ __forceinline__ void st2(float* p, float2 v) {
     *reinterpret_cast<float2*>(p) = v;
   }
+  static __device__ __forceinline__ void st2_sr(float* p, float2 v, unsigned) { st2(p, v); }
 };
 // Reduced-precision storage of the same deviations: loads widen to FP32, all
 // arithmetic is FP32, stores round to nearest.
+// Stochastic rounding of an FP32 pair to 16 bits (Blackwell's cvt.rs): each
+// value rounds up with probability equal to the fraction of the spacing it
+// lies above the lower neighbour, decided by the random bits rbits.  The
+// pair is packed with species a (the lower address) in the low half.
+__device__ __forceinline__ unsigned cvt_rs_bf16x2(float a, float b, unsigned rbits) {
+  unsigned d;
+  asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(b), "f"(a), "r"(rbits));
+  return d;
+}
+__device__ __forceinline__ unsigned cvt_rs_f16x2(float a, float b, unsigned rbits) {
+  unsigned d;
+  asm("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(b), "f"(a), "r"(rbits));
+  return d;
+}
+
 template <>
 struct Stor<__nv_bfloat16> {
   static __device__ __forceinline__ float ld(const __nv_bfloat16* p) {
@@ -279,6 +296,9 @@ struct Stor<__nv_bfloat16> {
   static __device__ __forceinline__ void st2(__nv_bfloat16* p, float2 v) {
     *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v);
   }
+  static __device__ __forceinline__ void st2_sr(__nv_bfloat16* p, float2 v, unsigned rbits) {
+    *reinterpret_cast<unsigned*>(p) = cvt_rs_bf16x2(v.x, v.y, rbits);
+  }
 };
 template <>
 struct Stor<__half> {
@@ -289,6 +309,9 @@ struct Stor<__half> {
   }
   static __device__ __forceinline__ void st2(__half* p, float2 v) {
     *reinterpret_cast<__half2*>(p) = __float22half2_rn(v);
+  }
+  static __device__ __forceinline__ void st2_sr(__half* p, float2 v, unsigned rbits) {
+    *reinterpret_cast<unsigned*>(p) = cvt_rs_f16x2(v.x, v.y, rbits);
   }
 };
 
@@ -385,7 +408,15 @@ __device__ __forceinline__ void pull_node(const ST* __restrict__ f, const Lat& L
     g[0] = ld(f, L, sp, 0, j, x);
     g[1] = fmaf(c1, dl, src(f, L, E, c1, sp, 1, j, xm));
     g[3] = fmaf(c1, dr, src(f, L, E, c1, sp, 3, j, xp));
-    if (bot) {
+    if (bot && L.wall_mode == LBM_WALL_BSR) {
+      // bounce-back (fraction r) and specular reflection (1 - r): the
+      // mirror image of c_5 = (1,1) leaves column x - 1 as c_8, that of c_6
+      // leaves column x + 1 as c_7
+      const float q = 1.0f - r_bot;
+      g[2] = ld(f, L, sp, 4, j, x);
+      g[5] = fmaf(r_bot, ld(f, L, sp, 7, j, x), q * fmaf(c5, dl, src(f, L, E, c5, sp, 8, j, xm)));
+      g[6] = fmaf(r_bot, ld(f, L, sp, 8, j, x), q * fmaf(c5, dr, src(f, L, E, c5, sp, 7, j, xp)));
+    } else if (bot) {
       float o4 = ld(f, L, sp, 4, j, x), o7 = ld(f, L, sp, 7, j, x), o8 = ld(f, L, sp, 8, j, x);
       // the equilibrium parts t/6, t/6 and t - 2 t/6 sum to t exactly up
       // to one rounding, so the wall conserves mass without an FP32 bias
@@ -398,7 +429,14 @@ __device__ __forceinline__ void pull_node(const ST* __restrict__ f, const Lat& L
       g[5] = fmaf(c5, dl, src(f, L, E, c5, sp, 5, j - 1, xm));
       g[6] = fmaf(c5, dr, src(f, L, E, c5, sp, 6, j - 1, xp));
     }
-    if (top) {
+    if (top && L.wall_mode == LBM_WALL_BSR) {
+      // mirror images: c_7 = (-1,-1) of c_6 from column x + 1, c_8 = (1,-1)
+      // of c_5 from column x - 1
+      const float q = 1.0f - r_top;
+      g[4] = ld(f, L, sp, 2, j, x);
+      g[7] = fmaf(r_top, ld(f, L, sp, 5, j, x), q * fmaf(c5, dr, src(f, L, E, c5, sp, 6, j, xp)));
+      g[8] = fmaf(r_top, ld(f, L, sp, 6, j, x), q * fmaf(c5, dl, src(f, L, E, c5, sp, 5, j, xm)));
+    } else if (top) {
       float o2 = ld(f, L, sp, 2, j, x), o5 = ld(f, L, sp, 5, j, x), o6 = ld(f, L, sp, 6, j, x);
       float t = r_top * (o2 + o5 + o6), q = 1.0f - r_top, t6 = t * (1.0f / 6.0f);
       g[4] = fmaf(q, o2, fmaf(-2.0f, t6, t));
@@ -588,8 +626,10 @@ __device__ __forceinline__ float tau_q_wall(const Lat& L, const Macro& m, float 
          dtt * (12.0f + 30.0f * tt * vs * A1) / (16.0f * tt * tt);
 }
 
-// r of Eq. R (first printed form) from the mixture molecular mass of the
-// reflected post-collision state at the wall node, c_m = c_m0 (2-alpha)/alpha.
+// r of Eq. R (first printed form), r = 2 - 2/(1 + X), from the mixture
+// molecular mass of the reflected post-collision state at the wall node,
+// c_m = c_m0 (2-alpha)/alpha; with the BSR wall the bounce-back fraction
+// 1/(1 + X) of the same slip factor X.
 template <typename ST>
 __device__ __forceinline__ float dbb_r(const Lat& L, const ColRef& C, const ST* __restrict__ f,
                                        int x, int j, float alpha) {
@@ -603,7 +643,8 @@ __device__ __forceinline__ float dbb_r(const Lat& L, const ColRef& C, const ST* 
   }
   float mx = (rho[0] + rho[1]) / fmaf(rho[0], L.s[0], rho[1] * L.s[1]);
   float cm = L.c_m0 * (2.0f - alpha) / alpha;
-  return 2.0f - 2.0f / (1.0f + cm * sqrtf(kPi * mx / 6.0f));
+  const float X = cm * sqrtf(kPi * mx / 6.0f);
+  return L.wall_mode == LBM_WALL_BSR ? 1.0f / (1.0f + X) : 2.0f - 2.0f / (1.0f + X);
 }
 
 // Density-correction factors of Eq. rho2 for the ghost columns, from the
@@ -647,29 +688,46 @@ struct WallSmem {
   float om_q[2][TX];
 };
 
-// Prologue of the step and moments kernels: warp ty = 0 handles the bottom
-// wall node of each column of the strip, warp ty = 1 the top one.
+// Prologue of the step and moments kernels for the CTA's rows
+// [j_begin, j_end): r of a wall is needed only by the CTA that holds that
+// wall's row, 1/tau_q of a wall only by CTAs with rows in that wall's half.
+// The four tasks run on four warps at once (ty = 0, 1: r of the bottom and
+// top wall; ty = 2, 3: their tau_q).  tau_q depends on the wall node's
+// pre-collision species densities only (through lambda and m_x), and the
+// DBB rule conserves each species' mass at the node whatever r is, so the
+// tau_q warps pull the wall node with r = 0 and need not wait for r (the
+// BSR rule moves mass between columns: there they evaluate r themselves).
 template <bool WITH_TQ, typename ST>
 __device__ __forceinline__ void wall_prologue(const Lat& L, const ST* __restrict__ fin,
                                               const float* __restrict__ alpha, const Ends& E,
-                                              const ColRef& C, int x, WallSmem& sm) {
+                                              const ColRef& C, int x, int j_begin, int j_end,
+                                              WallSmem& sm) {
   const int tx = threadIdx.x, ty = threadIdx.y;
-  if (ty < 2) {
-    float r = 1.0f, omq = 1.0f;
-    if (interior(L, x)) {
-      const int jw = ty == 0 ? 0 : L.N - 1;
-      float al = alpha[ty * L.Nx + x];
-      r = dbb_r(L, C, fin, x, jw, al);
-      if (WITH_TQ) {
+  if (ty < (WITH_TQ ? 4 : 2)) {
+    const int wall = ty & 1;
+    const bool tq = ty >= 2;
+    const int half = (L.N + 1) / 2;  // rows j < half use the bottom tau_q
+    const bool needed = tq ? (wall == 0 ? j_begin < half : j_end > half)
+                           : (wall == 0 ? j_begin == 0 : j_end == L.N);
+    float v = 1.0f;
+    if (needed && interior(L, x)) {
+      const int jw = wall == 0 ? 0 : L.N - 1;
+      const float al = alpha[wall * L.Nx + x];
+      if (!tq) {
+        v = dbb_r(L, C, fin, x, jw, al);
+      } else {
         float fs[2][9];
-        pull_node(fin, L, E, C, x, jw, r, r, fs);
+        const float rr = L.wall_mode == LBM_WALL_BSR ? dbb_r(L, C, fin, x, jw, al) : 0.0f;
+        pull_node(fin, L, E, C, x, jw, rr, rr, fs);
         Macro m;
         macro(L, C, fs, m);
-        omq = 1.0f / tau_q_wall(L, m, al);
+        v = 1.0f / tau_q_wall(L, m, al);
       }
     }
-    sm.r[ty][tx] = r;
-    sm.om_q[ty][tx] = omq;
+    if (tq)
+      sm.om_q[wall][tx] = v;
+    else
+      sm.r[wall][tx] = v;
   }
   __syncthreads();
 }
@@ -690,6 +748,25 @@ struct KahanF {
 };
 
 // ------------------------------------------------------------ step kernel
+// Random bits of the stochastic rounding: a 32-bit integer hash (the
+// "lowbias32" xorshift-multiply hash of C. Wellons) seeds one linear
+// congruential generator per thread and launch (multiplier 1664525 and
+// increment 1013904223, the quick generator of Numerical Recipes), whose
+// state is folded (high half into the low half) so that both 16-bit halves
+// of each word are usable.
+__device__ __forceinline__ unsigned hash32(unsigned x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+__device__ __forceinline__ unsigned lcg_next(unsigned& s) {
+  s = s * 1664525u + 1013904223u;
+  return s ^ (s >> 16);
+}
+
 template <typename ST>
 struct StepArgs {
   const ST* __restrict__ fin;     // post-collision deviations of step t-1
@@ -706,6 +783,8 @@ struct StepArgs {
   double* __restrict__ colpart;      // [R][4][Nx] per-row-block column sums (R > 1)
   unsigned* __restrict__ strip_cnt;  // [strips] row blocks finished this step
   int rows_per_block;                // rows of one row block (multiple of TY)
+  unsigned seed;                     // 16-bit storage: per-step seed of the
+                                     // stochastic rounding; 0 = round to nearest
 };
 
 struct RedSmem {
@@ -912,7 +991,7 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
   // the first row of each warp is read from L2 while the wall prologue runs
   if (tx == 0 && j_begin + ty < j_end)
     prefetch_row_l2(a.fin + (size_t)blockIdx.x * L.SS + (size_t)(j_begin + ty) * RS);
-  wall_prologue<true>(L, a.fin, a.alpha, E, C, x, wsm);
+  wall_prologue<true>(L, a.fin, a.alpha, E, C, x, j_begin, j_end, wsm);
   const bool in = interior(L, x);
   // strips holding column 1 or N_x - 2 take the general pull (ghost columns)
   const bool edge_strip = !L.x_periodic && (x0 <= 1 || x0 + TX > L.Nx - 2);
@@ -925,6 +1004,11 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
   const int half = (L.N + 1) / 2;  // rows j < half (1-based 2J <= N+1) use the bottom tau_q
   KahanF acc[4];
   const bool reduce = DIAG || edge_strip;
+  // per-thread generator of the stochastic rounding (16-bit storage only)
+  unsigned rng = sizeof(ST) < 4
+                     ? hash32(a.seed ^ hash32((blockIdx.y * gridDim.x + blockIdx.x) * (TX * TY) +
+                                             ty * TX + tx))
+                     : 0u;
   if (in) {
     for (int j = j_begin + ty; j < j_end; j += TY) {
       float2 g[9];
@@ -956,8 +1040,13 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
         acc[3].add(mxs.y);
       }
       ST* o = a.fout + base + j * RS;
+      if (sizeof(ST) < 4 && a.seed != 0u) {
 #pragma unroll
-      for (int i = 0; i < 9; ++i) Stor<ST>::st2(o + i * PS, g[i]);
+        for (int i = 0; i < 9; ++i) Stor<ST>::st2_sr(o + i * PS, g[i], lcg_next(rng));
+      } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Stor<ST>::st2(o + i * PS, g[i]);
+      }
     }
   }
   if (!reduce) return;  // CTA-uniform
@@ -987,7 +1076,7 @@ __global__ void __launch_bounds__(TX* TY)
   const int x = blockIdx.x * TX + tx;
   const ColRef C = col_ref(L, refrho, x);
   const Ends E = load_ends(L, cs_in, refrho);
-  if (!direct) wall_prologue<false>(L, fin, alpha, E, C, x, wsm);
+  if (!direct) wall_prologue<false>(L, fin, alpha, E, C, x, 0, L.N, wsm);
   if (!interior(L, x)) return;
   const size_t plane = (size_t)L.N * L.Nx;
   for (int j = ty; j < L.N; j += TY) {
@@ -1204,6 +1293,7 @@ struct lbm_mix {
   lbm_mix_params p;
   Lat L;
   int device;
+  int nsm;            // streaming multiprocessors of the device
   cudaStream_t stream;
   bool own_stream;
   int nblocks;
@@ -1264,6 +1354,10 @@ int validate(const lbm_mix_params* p, int* Nx_out) {
   if (p->x_periodic != 0 && p->x_periodic != 1) return set_err(LBM_EINVAL, "x_periodic is 0 or 1");
   if (p->diag_every < 1) return set_err(LBM_EINVAL, "diag_every must be >= 1");
   if (p->reref_every < -1) return set_err(LBM_EINVAL, "reref_every must be >= -1");
+  if (p->wall != LBM_WALL_DBB && p->wall != LBM_WALL_BSR)
+    return set_err(LBM_EINVAL, "wall must be LBM_WALL_DBB or LBM_WALL_BSR");
+  if (p->rounding != LBM_ROUND_STOCHASTIC && p->rounding != LBM_ROUND_NEAREST)
+    return set_err(LBM_EINVAL, "rounding must be LBM_ROUND_STOCHASTIC or LBM_ROUND_NEAREST");
   long pitch = (Nx + 31) / 32 * 32;
   double elems = 18.0 * (double)p->N * (double)pitch;
   if (elems >= 2147483648.0)
@@ -1283,6 +1377,7 @@ Lat derive(const lbm_mix_params* p, int Nx) {
   L.pitch = (Nx + 31) / 32 * 32;
   L.SS = (unsigned)((long)L.N * RS);
   L.x_periodic = p->x_periodic;
+  L.wall_mode = p->wall;
   double m_min = fmin(p->m_a, p->m_b);
   double mh[2] = {p->m_a / m_min, p->m_b / m_min};
   L.light = (p->m_a <= p->m_b) ? 0 : 1;
@@ -1340,6 +1435,16 @@ Lat derive(const lbm_mix_params* p, int Nx) {
   L.c_m0 = (float)p->c_m0;
   L.H = (float)p->N;
   return L;
+}
+
+// Host copy of the step kernel's seed hash (lowbias32).
+unsigned host_hash32(unsigned x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
 }
 
 // Rows of one strip per CTA of the step kernel unless the caller sets a
@@ -1455,6 +1560,10 @@ int launch_step(lbm_mix* h, bool diag) {
     a.colpart = h->colpart;
     a.strip_cnt = h->strip_cnt;
     a.rows_per_block = h->rows_per_block;
+    // stochastic rounding of 16-bit stores: a fresh seed every step (never 0)
+    a.seed = (sizeof(ST) < 4 && h->p.rounding == LBM_ROUND_STOCHASTIC)
+                 ? (host_hash32((unsigned)(h->steps + 1)) | 1u)
+                 : 0u;
     dim3 blk(TX, TY), grd(h->nblocks, h->R);
     if (diag)
       lbm_step_kernel<ST, true><<<grd, blk, 0, h->stream>>>(h->L, a);
@@ -1524,23 +1633,48 @@ constexpr size_t NOALLOC_CNT_WORDS = NOALLOC_MAX_STRIPS + 4;
 constexpr size_t NOALLOC_DOUBLES = NOALLOC_PART_DOUBLES + (NOALLOC_CNT_WORDS + 1) / 2;
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
 
-// Device address of g_noalloc_scratch for the current device, looked up once
-// per device.  In host code the symbol's name only stands for the device
-// array; kernels must be given this address.
+// The calling thread's current CUDA context (the driver's cuCtxGetCurrent,
+// reached through the runtime so that the library needs no link against
+// the driver library); nullptr if none is current or the query fails.
+void* current_context() {
+  typedef int (*CtxGetCurrent)(void**);
+  static CtxGetCurrent fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return (CtxGetCurrent)f;
+  }();
+  void* ctx = nullptr;
+  if (!fn || fn(&ctx) != 0) return nullptr;
+  return ctx;
+}
+
+// Device address of g_noalloc_scratch in the current device's context.  In
+// host code the symbol's name only stands for the device array; kernels
+// must be given this address.  It is looked up on the first call on a
+// device and again whenever the current context is not the one it was
+// looked up in (a device reset or another primary context loads the module
+// anew, at another address).
 int noalloc_scratch_address(double** out) {
   static std::mutex mu;
   static double* addr[64] = {};
+  static void* ctx_of[64] = {};
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return set_err(LBM_EINVAL, "device ordinal %d out of range", dev);
   std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
+  void* ctx = current_context();
+  if (!addr[dev] || !ctx || ctx != ctx_of[dev]) {
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess || !ptr)
       return set_err(LBM_ECUDA, "cudaGetSymbolAddress(scratch) failed on device %d: %s", dev,
                      cudaGetErrorString(e));
     addr[dev] = (double*)ptr;
+    ctx_of[dev] = current_context();  // the lookup made the primary context current
   }
   *out = addr[dev];
   return LBM_OK;
@@ -1595,6 +1729,8 @@ void lbm_mix_default_params(lbm_mix_params* p) {
   p->x_periodic = 0;
   p->diag_every = 1;
   p->reref_every = -1;
+  p->rounding = LBM_ROUND_STOCHASTIC;
+  p->wall = LBM_WALL_DBB;
 }
 
 const char* lbm_mix_strerror(int s) {
@@ -1654,7 +1790,8 @@ int lbm_mix_create(const lbm_mix_params* p, void* stream, lbm_mix** out) {
   memset(h, 0, sizeof *h);
   h->p = *p;
   h->L = derive(p, Nx);
-  if (cudaGetDevice(&h->device) != cudaSuccess) {
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
     delete h;
     return set_err(LBM_ECUDA, "no CUDA device");
   }
@@ -1689,8 +1826,8 @@ int lbm_mix_create(const lbm_mix_params* p, void* stream, lbm_mix** out) {
   ALLOC(h->diag_count, sizeof(unsigned long long));
   ALLOC(h->clprof, sizeof(double) * (size_t)Nx);
   // Row blocks: split each strip's rows over R CTAs of DEFAULT_ROWS rows so
-  // that the grid holds many waves of CTAs on 152 SMs and its last, partial
-  // wave is a small share of the launch.
+  // that the grid holds many waves of CTAs on the device's SMs and its last,
+  // partial wave is a small share of the launch.
   h->rows_per_block = default_rows(h->L.N);
   h->R = (h->L.N + h->rows_per_block - 1) / h->rows_per_block;
   h->R_alloc = h->R;
@@ -2050,6 +2187,7 @@ int lbm_mix_step_noalloc(const lbm_mix_params* p, const float* d_in, float* d_ou
   a.clprof = d_cl_profile;
   a.colpart = nullptr;  // one row block per strip: no row-block partials
   a.rows_per_block = (L.N + TY - 1) / TY * TY;
+  a.seed = 0u;  // FP32 storage: no rounding to 16 bits
   dim3 blk(TX, TY), grd(nstrips, 1);
   lbm_step_kernel<float, true><<<grd, blk, 0, s>>>(L, a);
   CK(cudaGetLastError());
@@ -2069,16 +2207,44 @@ int lbm_mix_step_noalloc(const lbm_mix_params* p, const float* d_in, float* d_ou
 // schedule (rows per CTA): each candidate schedule runs one real block of
 // steps, the fastest is kept.  Schedules change only the order of the FP64
 // column reductions, not the time integration.
+// What a captured graph has baked into its launches besides the handle's
+// fixed buffers: the buffer parity it starts from, the schedule (rows per
+// CTA, row blocks and their partials), the reference-density table (swapped
+// by re-referencing) and the step phase that decides which captured steps
+// reduce diagnostics.  A graph is replayed only while all of them match.
+struct SweepCapKey {
+  int cur, rows, R;
+  const void* colpart;
+  const void* refrho;
+  long phase;
+};
+
 struct lbm_sweep {
   int n = 0;
   lbm_mix** h = nullptr;
   cudaGraphExec_t* exec = nullptr;
   long* exec_K = nullptr;  // steps captured in exec[i]; 0 = none
+  SweepCapKey* key = nullptr;  // state each graph was captured from
   int policy = -1;         // schedule in use (-1: the library default)
   double round_ms[LBM_SWEEP_NPOLICY] = {};
 };
 
 namespace {
+
+SweepCapKey cap_key(const lbm_mix* h) {
+  return SweepCapKey{h->cur, h->rows_per_block, h->R, h->colpart, h->refrho,
+                     h->steps % h->p.diag_every};
+}
+
+bool same_key(const SweepCapKey& a, const SweepCapKey& b) {
+  return a.cur == b.cur && a.rows == b.rows && a.R == b.R && a.colpart == b.colpart &&
+         a.refrho == b.refrho && a.phase == b.phase;
+}
+
+// Instance i has a graph of K steps that is valid for its current state.
+bool graph_valid(const lbm_sweep* s, int i, long K) {
+  return s->exec[i] && s->exec_K[i] == K && same_key(s->key[i], cap_key(s->h[i]));
+}
 
 // Rows per CTA of instance h under schedule policy p.
 int policy_rows(const lbm_mix* h, int p) {
@@ -2089,7 +2255,7 @@ int policy_rows(const lbm_mix* h, int p) {
     case 2: return 32;
     case 3: return 16;
     default: {  // fill: about two CTAs per SM for this instance alone
-      const long want = 2L * 152;
+      const long want = 2L * (h->nsm > 0 ? h->nsm : 1);
       long rows = ((long)N * h->nblocks + want - 1) / want;
       rows = (rows + TY - 1) / TY * TY;
       if (rows < 16) rows = 16;
@@ -2113,6 +2279,7 @@ int capture_steps(lbm_sweep* s, int i, long K) {
   drop_graph(s, i);
   const long steps0 = h->steps;
   const int cur0 = h->cur;
+  const SweepCapKey key = cap_key(h);
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   int st = lbm_mix_step(h, K);
   cudaGraph_t g = nullptr;
@@ -2132,6 +2299,7 @@ int capture_steps(lbm_sweep* s, int i, long K) {
     return set_err(LBM_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
   }
   s->exec_K[i] = K;
+  s->key[i] = key;
   return LBM_OK;
 }
 
@@ -2177,7 +2345,8 @@ int lbm_sweep_create(const lbm_mix_params* params, int n, lbm_sweep** out) {
   s->h = (lbm_mix**)calloc(n, sizeof(lbm_mix*));
   s->exec = (cudaGraphExec_t*)calloc(n, sizeof(cudaGraphExec_t));
   s->exec_K = (long*)calloc(n, sizeof(long));
-  if (!s->h || !s->exec || !s->exec_K) {
+  s->key = (SweepCapKey*)calloc(n, sizeof(SweepCapKey));
+  if (!s->h || !s->exec || !s->exec_K || !s->key) {
     lbm_sweep_destroy(s);
     return set_err(LBM_ENOMEM, "host allocation failed");
   }
@@ -2204,6 +2373,7 @@ void lbm_sweep_destroy(lbm_sweep* s) {
   free(s->h);
   free(s->exec);
   free(s->exec_K);
+  free(s->key);
   delete s;
 }
 
@@ -2259,8 +2429,11 @@ int lbm_sweep_run_to_steady(lbm_sweep* s, double tol, long max_steps, long check
     // the captured length, plain launches for a shorter last block
     const long left = max_steps - taken[act[0]];
     const long k = check_every < left ? check_every : left;
+    // (re)capture where no graph exists or the state moved away from the one
+    // it was captured from (odd step counts, state uploads, schedule changes,
+    // re-referencing through the borrowed handle)
     for (int a = 0; a < na && !st; ++a)
-      if (k == check_every && s->exec_K[act[a]] != k) st = capture_steps(s, act[a], k);
+      if (k == check_every && !graph_valid(s, act[a], k)) st = capture_steps(s, act[a], k);
     if (st) break;
     const double t0 = now_ms();
     for (int a = 0; a < na && !st; ++a) {

@@ -156,6 +156,26 @@ def test_checkpoint_interval_does_not_change_the_gradient():
         assert np.array_equal(g["alpha"], out[0]["alpha"])
 
 
+@pytest.mark.parametrize("steps,ckpt", [(300, 7), (301, 7), (300, 30), (10, 4)])
+def test_state_is_kept_through_the_gradient(steps, ckpt):
+    """The backward sweep replays every checkpoint interval; the final state
+    of the forward run must survive it, whatever the parity of the step count
+    and whether the interval divides it."""
+    al = _alpha(SMALL["N_x"])
+    a = binding.LbmAdjoint(SMALL, steps, ckpt, al)
+    a.forward()
+    before = a.state()
+    a.gradient(binding.LBM_ADJ_CL)
+    assert np.array_equal(a.state(), before)
+    o = oracle.Oracle(SMALL)
+    o.init()
+    o.set_accommodation_field(np.ascontiguousarray(al.ravel()))
+    o.step(steps)
+    Fo = o.get_post_state()
+    inner = np.s_[..., 1:-1]
+    assert np.abs(before[inner] - Fo[inner]).max() <= 1e-11 * np.abs(Fo[inner]).max()
+
+
 def test_autograd_function():
     torch = pytest.importorskip("torch")
     from paper_1603_08221_gb300.autograd import channel_objective

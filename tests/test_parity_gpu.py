@@ -351,3 +351,23 @@ def test_zero_steps_leave_the_initial_state():
     F = g.get_post_state_f64()
     Fo = o.get_post_state()
     assert _relerr(F[..., 1:-1], Fo[..., 1:-1]) < RTOL_RHO
+
+
+@pytest.mark.parametrize("N,Nx,steps,x_periodic", [(8, 8, 100, 0), (20, 100, 300, 0),
+                                                    (8, 40, 200, 1)])
+def test_bsr_wall(N, Nx, steps, x_periodic):
+    """The bounce-back / specular-reflection wall (LBM_WALL_BSR): the
+    specular partners come from the neighbour columns, through the ghost
+    columns of the pressure ends at columns 1 and N_x - 2 and across the
+    periodic seam; a per-wall-node accommodation field varies r_b along the
+    walls."""
+    p = workloads.preset("heli_argon_320x16", N=N, N_x=Nx, theta=1.5, wall=binding.LBM_WALL_BSR,
+                         x_periodic=x_periodic)
+    alpha = workloads.random_accommodation(Nx, seed=5, spread=0.2)
+    g, o = _pair(p, steps, alpha=alpha)
+    _check_moments(g, o)
+    fp_g = g.get_post_state_f64()[..., 1:-1]
+    fp_o = o.get_post_state()[..., 1:-1]
+    assert _relerr(fp_g, fp_o) < RTOL_RHO
+    sg, so = g.separation(), o.separation()
+    assert abs(sg["CL"] - so["CL"]) < 1e-3 * max(abs(so["CL"]), 1e-4)

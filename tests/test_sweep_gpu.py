@@ -130,3 +130,52 @@ def test_sweep_with_no_steps():
     assert steps == [0, 0] and status == [binding.LBM_ENOTCONVERGED] * 2
     with pytest.raises(binding.LbmError):
         sw.run_to_steady(1e-7, 1000, 501)  # odd check interval: no whole graphs
+
+
+
+def _same_sequence(run, handles):
+    """run_to_steady (run()), then on every handle a change of what captured
+    sweep graphs bake in, then run_to_steady again; returns the outcomes."""
+    out = [run()]
+    for h in handles:
+        h.step(1)  # odd: the buffer parity flips under any captured graph
+    out.append(run())
+    for h in handles:
+        h.set_post_state(h.get_post_state())  # upload: parity reset to buffer 0
+    out.append(run())
+    for h in handles:
+        h.set_rows_per_block(16)  # schedule: the row-block partials are reallocated
+    out.append(run())
+    for h in handles:
+        h.rereference()  # the reference-density table swaps
+    out.append(run())
+    return out
+
+
+def test_sweep_graphs_follow_state_changes():
+    """A captured graph bakes in the buffer parity, schedule and reference
+    table of the state it was captured from; calls on the borrowed handles
+    that change them between run_to_steady calls must lead to a recapture,
+    so that every instance still takes exactly the steps of a lone handle
+    driven through the same calls (bitwise the same state)."""
+    params = SMALL[:2]
+    sw = binding.LbmSweep(params)
+    sw.init()
+    insts = [sw.instance(k) for k in range(len(params))]
+
+    def run_sweep():
+        return [tuple(v) for v in zip(*sw.run_to_steady(1e-12, 1000, 500, autotune=False))]
+    swept = _same_sequence(run_sweep, insts)
+    for k, p in enumerate(params):
+        g = binding.LbmMix(**p)
+        g.init()
+
+        def run_lone(g=g):
+            st, n, r = g.run_to_steady(1e-12, 1000, 500)
+            return (n, r, st)
+        lone = _same_sequence(run_lone, [g])
+        assert [o[k] for o in swept] == lone, k
+        m, mg = insts[k].moments(), g.moments()
+        for key in m:
+            assert np.array_equal(m[key], mg[key]), (k, key)
+        assert insts[k].separation()["CL"] == g.separation()["CL"]
