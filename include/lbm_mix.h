@@ -67,6 +67,16 @@ extern "C" {
 #define LBM_WALL_DBB 0 /* default */
 #define LBM_WALL_BSR 1
 
+/* Readings of Eq. R, whose two printed forms disagree for unequal masses
+ * (masses in units of m_min; all three agree when m_a = m_b):
+ * r_s = 2 - 2/(1 + X_s) with X_s = c_m sqrt(pi m_x / 6) for both species
+ * (the first form, the default), c_m sqrt(pi m_x / (6 m_s)) (m_min of the
+ * first form replaced by the species mass) or c_m sqrt(pi m_x^2 / (6 m_s))
+ * (the second form, with m_r = m_s / m_x). */
+#define LBM_R_FIRST 0
+#define LBM_R_SPECIES 1
+#define LBM_R_SECOND 2
+
 typedef struct lbm_mix lbm_mix; /* opaque, owned by the library */
 
 /* Physical problem (Sec. 2, Table 1) and model knobs (Sec. 3). */
@@ -93,13 +103,18 @@ typedef struct {
   int rounding;         /* BF16/FP16 stores: LBM_ROUND_STOCHASTIC or LBM_ROUND_NEAREST
                            (FP32 storage ignores it) */
   int wall;             /* LBM_WALL_DBB or LBM_WALL_BSR */
+  int r_form;           /* LBM_R_FIRST, LBM_R_SPECIES or LBM_R_SECOND (Eq. R) */
+  int lambda_pressure;  /* species mean free path lambda_s = (mu_s / p') sqrt(pi
+                           k_B T / (2 m_s)) with p' the partial pressure x_s p
+                           (0, default) or the mixture pressure p (1) */
 } lbm_mix_params;
 
 /* Fills the defaults: He-Ar (4.003, 39.948), C_l = 0.5, C_l_out = -1,
  * theta = 2, Kn_out = 0.1, N = 16, N_x = 0, L_over_H = 20, alpha = 1,
  * c_m0 = 1.016, tau_rho = 1, tau_e = 1.1, tau_eps = 1.2, mu ratios 1,
  * LBM_FP32, x_periodic = 0, diag_every = 1, reref_every = -1,
- * rounding = LBM_ROUND_STOCHASTIC, wall = LBM_WALL_DBB.  NULL-safe. */
+ * rounding = LBM_ROUND_STOCHASTIC, wall = LBM_WALL_DBB, r_form = LBM_R_FIRST,
+ * lambda_pressure = 0.  NULL-safe. */
 void lbm_mix_default_params(lbm_mix_params* p);
 
 /* Validates p, derives the lattice constants (Eqs. P, EQFrb, rho2 with the
@@ -380,9 +395,10 @@ typedef struct lbm_adj lbm_adj;
 #define LBM_ADJ_FLUX 1
 
 /* Validates p like lbm_mix_create (storage is ignored: FP64; x_periodic
- * channels and the BSR wall are rejected: the adjoint covers the
- * pressure-driven channel with its inlet and outlet, Eqs. rho1 and rho2,
- * between DBB walls) and allocates
+ * channels, the BSR wall and the non-default readings r_form and
+ * lambda_pressure are rejected: the adjoint covers the pressure-driven
+ * channel with its inlet and outlet, Eqs. rho1 and rho2, between DBB walls,
+ * with the default readings) and allocates
  * the checkpoints (ceil(nsteps/checkpoint_every) + 1 states of 18 N N_x
  * doubles) and one interval of replayed states.  stream: cudaStream_t or
  * NULL for an own stream.  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */

@@ -51,7 +51,7 @@ class OrcParams(ctypes.Structure):
         ("tau_eps", ctypes.c_double),
         ("mu_ratio_a", ctypes.c_double), ("mu_ratio_b", ctypes.c_double),
         ("x_periodic", ctypes.c_int), ("y_periodic", ctypes.c_int),
-        ("psi_off", ctypes.c_int), ("r_mode", ctypes.c_int), ("lam_mode", ctypes.c_int),
+        ("psi_off", ctypes.c_int), ("r_form", ctypes.c_int), ("lambda_pressure", ctypes.c_int),
         ("store_fmt", ctypes.c_int), ("store_sr", ctypes.c_int), ("reref_every", ctypes.c_int),
         ("store_seed", ctypes.c_uint), ("wall", ctypes.c_int),
     ]
@@ -170,7 +170,7 @@ def set_num_threads(n: int) -> None:
 
 _DEFAULTS = dict(C_l_out=-1.0, accommodation=1.0, c_m0=1.016, tau_rho=1.0,
                  tau_e=1.1, tau_eps=1.2, mu_ratio_a=1.0, mu_ratio_b=1.0,
-                 x_periodic=0, y_periodic=0, psi_off=0, r_mode=0, lam_mode=0,
+                 x_periodic=0, y_periodic=0, psi_off=0, r_form=0, lambda_pressure=0,
                  store_fmt=0, store_sr=0, reref_every=0, store_seed=0, wall=0)
 
 

@@ -99,15 +99,15 @@ typedef struct {
   /* Readings knobs (0 = the default reading everywhere):
    *  psi_off   1: Psi = 1 (unbounded mean free path, no wall-confinement
    *             correction), so tau'_s(0) = 0 in Eq. taoq (test mode);
-   *  r_mode    Eq. R: 0 first printed form, one r for both species with
+   *  r_form    Eq. R: 0 first printed form, one r for both species with
    *             sqrt(pi m_x / (6 m_min)); 1 species form sqrt(pi m_x /
    *             (6 m_sigma)); 2 second printed form with m_r = m_sigma/m_x
    *             and masses in units of m_min, sqrt(pi m_x^2 / (6 m_sigma));
-   *  lam_mode  lambda_sigma: 0 with the partial pressure p_sigma = x_sigma p;
+   *  lambda_pressure  lambda_sigma: 0 with the partial pressure p_sigma = x_sigma p;
    *             1 with the mixture pressure p. */
   int psi_off;
-  int r_mode;
-  int lam_mode;
+  int r_form;
+  int lambda_pressure;
   /* Storage emulation (test mode, not part of the method): 0 none; else the
    * post-collision populations of every updated node are kept as deviations
    * from the rest equilibrium w_i alpha_si rhobar_s(x) of a per-column
@@ -341,7 +341,7 @@ static void node_moments(const orc_sim *S, const double fa[Q], const double fb[Q
    * after Eq. EQFrsp), with the partial pressure for each species */
   ns->lam = S->mu / ns->p * sqrt(PI * S->kT / (2.0 * ns->mx));
   for (int sp = 0; sp < 2; ++sp) {
-    double p_s = S->p.lam_mode == 1 ? ns->p : ns->x_s[sp] * ns->p;
+    double p_s = S->p.lambda_pressure == 1 ? ns->p : ns->x_s[sp] * ns->p;
     ns->lam_s[sp] = S->mu_s[sp] / p_s * sqrt(PI * S->kT / (2.0 * S->mh[sp]));
   }
   const double H = (double)S->N;
@@ -386,14 +386,14 @@ double orc_tau_s_tilde(double y, double H, double lam, double mx) {
 }
 
 /* The slip factor X of Eq. R, r_sigma = 2 - 2/(1 + X), with c_m = c_m0
- * (2 - alpha)/alpha.  r_mode 0: the first printed form, the same for both
+ * (2 - alpha)/alpha.  r_form 0: the first printed form, the same for both
  * species; 1: m_min replaced by m_sigma; 2: the second printed form with
  * m_r = m_sigma / m_x (masses in units of m_min).  All three agree when
  * m_a = m_b. */
 static double slip_X(const orc_sim *S, double mx_w, double alpha, int sp) {
   double cm = S->p.c_m0 * (2.0 - alpha) / alpha;
-  if (S->p.r_mode == 1) return cm * sqrt(PI * mx_w / (6.0 * S->mh[sp]));
-  if (S->p.r_mode == 2) return cm * sqrt(PI * mx_w / (6.0 * (S->mh[sp] / mx_w)));
+  if (S->p.r_form == 1) return cm * sqrt(PI * mx_w / (6.0 * S->mh[sp]));
+  if (S->p.r_form == 2) return cm * sqrt(PI * mx_w / (6.0 * (S->mh[sp] / mx_w)));
   return cm / 3.0 * sqrt(PI * mx_w / (2.0 * S->kT));
 }
 
@@ -470,6 +470,7 @@ static double cw_of(const orc_sim *S, int sp, int i) {
 static void emulate_storage(orc_sim *S) {
   const int N = S->N, Nx = S->Nx, fmt = S->p.store_fmt;
   const uint64_t step = (uint64_t)S->steps;
+#pragma omp parallel for collapse(2) schedule(static)
   for (int sp = 0; sp < 2; ++sp)
     for (int x = 0; x < Nx; ++x) {
       if (!is_interior_col(S, x)) continue;
@@ -507,8 +508,8 @@ orc_sim *orc_create(const orc_params *p) {
         p->Kn_out > 0 && p->N >= 2 && p->N_x >= 4 && p->accommodation > 0 &&
         p->accommodation <= 1 && p->tau_rho > 0.5 && p->tau_e > 0.5 &&
         p->tau_eps > 0.5 && p->mu_ratio_a > 0 && p->mu_ratio_b > 0 &&
-        (p->psi_off == 0 || p->psi_off == 1) && p->r_mode >= 0 && p->r_mode <= 2 &&
-        (p->lam_mode == 0 || p->lam_mode == 1) && p->store_fmt >= 0 && p->store_fmt <= 3 &&
+        (p->psi_off == 0 || p->psi_off == 1) && p->r_form >= 0 && p->r_form <= 2 &&
+        (p->lambda_pressure == 0 || p->lambda_pressure == 1) && p->store_fmt >= 0 && p->store_fmt <= 3 &&
         (p->store_sr == 0 || p->store_sr == 1) && p->reref_every >= 0 &&
         (p->wall == 0 || p->wall == 1)))
     return NULL;
@@ -674,7 +675,9 @@ static void stream_and_bound(orc_sim *S) {
     }
   }
   /* Push: every source node (including the ghost columns) sends f'_i to
-   * x + c_i; destinations outside the interior are dropped. */
+   * x + c_i; destinations outside the interior are dropped.  Each (species,
+   * population) pair writes its own plane, so the pairs run in parallel. */
+#pragma omp parallel for collapse(2) schedule(static)
   for (int sp = 0; sp < 2; ++sp)
     for (int i = 0; i < Q; ++i)
       for (int j = 0; j < N; ++j)

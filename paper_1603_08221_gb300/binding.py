@@ -31,6 +31,9 @@ LBM_ROUND_STOCHASTIC = 0
 LBM_ROUND_NEAREST = 1
 LBM_WALL_DBB = 0
 LBM_WALL_BSR = 1
+LBM_R_FIRST = 0
+LBM_R_SPECIES = 1
+LBM_R_SECOND = 2
 
 
 class lbm_mix_params(ctypes.Structure):
@@ -49,6 +52,7 @@ class lbm_mix_params(ctypes.Structure):
         ("reref_every", ctypes.c_int),
         ("rounding", ctypes.c_int),
         ("wall", ctypes.c_int),
+        ("r_form", ctypes.c_int), ("lambda_pressure", ctypes.c_int),
     ]
 
 

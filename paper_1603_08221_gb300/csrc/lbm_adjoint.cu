@@ -997,6 +997,9 @@ int lbm_adj_create(const lbm_mix_params* p, long nsteps, int checkpoint_every, v
     return lbm_internal_error(LBM_EINVAL, "the adjoint covers channels with pressure ends only");
   if (p->wall != LBM_WALL_DBB)
     return lbm_internal_error(LBM_EINVAL, "the adjoint covers the diffuse bounce-back wall only");
+  if (p->r_form != LBM_R_FIRST || p->lambda_pressure != 0)
+    return lbm_internal_error(LBM_EINVAL, "the adjoint covers the default readings of Eq. R and "
+                                          "of lambda_sigma only");
   lbm_adj* a = new (std::nothrow) lbm_adj;
   if (!a) return lbm_internal_error(LBM_ENOMEM, "host allocation failed");
   a->p = *p;

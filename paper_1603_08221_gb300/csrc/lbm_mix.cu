@@ -76,6 +76,9 @@ struct Lat {
   unsigned SS;           // floats per strip: N * RS
   int x_periodic;
   int wall_mode;         // LBM_WALL_DBB or LBM_WALL_BSR
+  int r_form;            // LBM_R_FIRST, LBM_R_SPECIES or LBM_R_SECOND (Eq. R)
+  int lam_mix;           // lambda_s with the mixture (1) or partial (0) pressure
+  float rsqrt_mh[2];     // 1 / sqrt(m_s / m_min)
   int light;             // index of the light species
   float s[2];            // s_sigma = m_min / m_sigma
   float cw0[2];          // rest-equilibrium weights w_i alpha_si: rest (9 - 5s)/9,
@@ -187,14 +190,14 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
   return __ffma2_rn(b, f2(-1.0f), a);  // exact: a - b with one rounding
 }
 
-// psi at two arguments at once.  The lanes of a warp sweep one row (the same
-// y) of 32 neighbouring columns, whose mean free paths differ little, so with
-// SKIP the two formulas of psi_dev are taken as warp-uniform branches: the
-// entire-part series when some lane has an argument <= 1, the rational form
-// when some lane has one in (1, 16).  Without SKIP both are evaluated and
-// selected (straight-line code that the compiler can interleave with the
-// loads of a memory-bound sweep).  At a >= 16, 1 - psi(a) < 2 e^{-a}/a <
-// 2^{-25} rounds away and psi = 1.
+// psi at two positive arguments at once.  The lanes of a warp sweep one row
+// (the same y) of 32 neighbouring columns, whose mean free paths differ
+// little, so with SKIP the two formulas of psi_dev are taken as warp-uniform
+// branches: the entire-part series when some lane has an argument <= 1, the
+// rational form when some lane has one in (1, 16).  Without SKIP both are
+// evaluated and selected (straight-line code that the compiler can
+// interleave with the loads of a memory-bound sweep).  At a >= 16,
+// 1 - psi(a) < 2 e^{-a}/a < 2^{-25} rounds away and psi = 1.
 template <bool SKIP>
 __device__ __forceinline__ float2 psi2(float2 a) {
   const bool small = (a.x <= 1.0f) || (a.y <= 1.0f);
@@ -223,7 +226,9 @@ __device__ __forceinline__ float2 psi2(float2 a) {
     ps = fma2(mul2(as, as), lg, mul2(q, as));
   }
   if (do_mid) {
-    const float2 al = make_float2(fmaxf(a.x, 1.0f), fmaxf(a.y, 1.0f));
+    // the argument is clamped to [1, 16]: at 16 the formula gives 1 in FP32
+    // (1 - psi(16) < 2^-25), and larger arguments cannot overflow it
+    const float2 al = make_float2(fminf(fmaxf(a.x, 1.0f), 16.0f), fminf(fmaxf(a.y, 1.0f), 16.0f));
     float2 num = add2(al, f2(8.5733287401f));
     num = fma2(num, al, f2(18.0590169730f));
     num = fma2(num, al, f2(8.6347608925f));
@@ -237,8 +242,8 @@ __device__ __forceinline__ float2 psi2(float2 a) {
     // 1 + e^{-a} [(a - 1) - a R]
     pl = fma2(e, fma2(make_float2(-al.x, -al.y), R, add2(al, f2(-1.0f))), f2(1.0f));
   }
-  return make_float2(a.x <= 1.0f ? (a.x > 0.0f ? ps.x : 0.0f) : (a.x < 16.0f ? pl.x : 1.0f),
-                     a.y <= 1.0f ? (a.y > 0.0f ? ps.y : 0.0f) : (a.y < 16.0f ? pl.y : 1.0f));
+  // arguments are y / lambda > 0 (y >= 1/2)
+  return make_float2(a.x <= 1.0f ? ps.x : pl.x, a.y <= 1.0f ? ps.y : pl.y);
 }
 
 // ------------------------------------------------------------- storage
@@ -392,8 +397,8 @@ __device__ __forceinline__ ColRef col_ref(const Lat& L, const float* __restrict_
 // d_i = (1 - r) d'_opp(i) + r (w_i/(1/6)) sum_outgoing d'.
 template <typename ST>
 __device__ __forceinline__ void pull_node(const ST* __restrict__ f, const Lat& L, const Ends& E,
-                                          const ColRef& C, int x, int j, float r_bot,
-                                          float r_top, float fs[2][9]) {
+                                          const ColRef& C, int x, int j, float2 r_bot2,
+                                          float2 r_top2, float fs[2][9]) {
   int xm = x - 1, xp = x + 1;
   if (L.x_periodic) {
     if (xm < 0) xm += L.Nx;
@@ -405,6 +410,7 @@ __device__ __forceinline__ void pull_node(const ST* __restrict__ f, const Lat& L
     float* g = fs[sp];
     const float c1 = L.cw1[sp], c5 = L.cw5[sp];
     const float dl = C.dl[sp], dr = C.dr[sp];
+    const float r_bot = sp ? r_bot2.y : r_bot2.x, r_top = sp ? r_top2.y : r_top2.x;
     g[0] = ld(f, L, sp, 0, j, x);
     g[1] = fmaf(c1, dl, src(f, L, E, c1, sp, 1, j, xm));
     g[3] = fmaf(c1, dr, src(f, L, E, c1, sp, 3, j, xp));
@@ -536,14 +542,19 @@ __device__ __forceinline__ void rates2(const Lat& L, const Macro2& m, float y, f
   const float lam = L.c_lam * m.inv_n * rs_mx;                // mixture mean free path
   const float inv_lam = L.inv_c_lam * m.n * (m.mx * rs_mx);  // 1 / lambda
   const float2 yy = make_float2(y, L.H - y);
-  const float2 inv_ls = mul2(mul2(m.rho, L.s2), L.inv_c_xl2);  // 1 / lambda_s
+  // 1 / lambda_s: n_s / c_xl with the partial pressure, n / c_xl with the
+  // mixture pressure
+  const float2 ns = mul2(m.rho, L.s2);
+  const float2 inv_ls = mul2(L.lam_mix ? f2(m.n) : ns, L.inv_c_xl2);
   const float2 pm = psi2<SKIP>(mul2(yy, f2(inv_lam)));
   const float2 pa = psi2<SKIP>(mul2(yy, f2(inv_ls.x)));
   const float2 pb = psi2<SKIP>(mul2(yy, f2(inv_ls.y)));
   const float ts = lam * (0.5f * (pm.x + pm.y)) * L.c_ts * rs_mx;  // tau_s - 1/2
   om_s = __fdividef(1.0f, 0.5f + ts);
-  // x_s lambda_se = c_xl / n * Psi(y; lambda_s)
-  const float2 xle = mul2(mul2(L.c_xl2, f2(0.5f * m.inv_n)),
+  // x_s lambda_se = c_xl / n * Psi(y; lambda_s) (partial pressure), times
+  // x_s = n_s / n with the mixture pressure
+  const float2 xs = L.lam_mix ? mul2(ns, f2(m.inv_n)) : f2(1.0f);
+  const float2 xle = mul2(mul2(mul2(L.c_xl2, f2(0.5f * m.inv_n)), xs),
                           make_float2(pa.x + pa.y, pb.x + pb.y));
   const float br = rsqrtf(xle.x) + rsqrtf(xle.y);
   // tau_d = 1/2 + c_td / (m_x br^2)  =>  1/tau_d = d / (d/2 + c_td), d = m_x br^2
@@ -626,13 +637,16 @@ __device__ __forceinline__ float tau_q_wall(const Lat& L, const Macro& m, float 
          dtt * (12.0f + 30.0f * tt * vs * A1) / (16.0f * tt * tt);
 }
 
-// r of Eq. R (first printed form), r = 2 - 2/(1 + X), from the mixture
-// molecular mass of the reflected post-collision state at the wall node,
-// c_m = c_m0 (2-alpha)/alpha; with the BSR wall the bounce-back fraction
-// 1/(1 + X) of the same slip factor X.
+// r of Eq. R, r = 2 - 2/(1 + X), from the mixture molecular mass of the
+// reflected post-collision state at the wall node, c_m = c_m0
+// (2-alpha)/alpha, for both species: X = c_m sqrt(pi m_x/6) (first printed
+// form, the same for both species; masses in units of m_min), c_m sqrt(pi
+// m_x/(6 m_s)) (m_min replaced by the species mass) or c_m sqrt(pi m_x^2/(6
+// m_s)) (second printed form, m_r = m_s/m_x).  With the BSR wall the
+// bounce-back fraction 1/(1 + X) of the same slip factor X.
 template <typename ST>
-__device__ __forceinline__ float dbb_r(const Lat& L, const ColRef& C, const ST* __restrict__ f,
-                                       int x, int j, float alpha) {
+__device__ __forceinline__ float2 dbb_r(const Lat& L, const ColRef& C, const ST* __restrict__ f,
+                                        int x, int j, float alpha) {
   float rho[2];
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
@@ -643,8 +657,14 @@ __device__ __forceinline__ float dbb_r(const Lat& L, const ColRef& C, const ST* 
   }
   float mx = (rho[0] + rho[1]) / fmaf(rho[0], L.s[0], rho[1] * L.s[1]);
   float cm = L.c_m0 * (2.0f - alpha) / alpha;
-  const float X = cm * sqrtf(kPi * mx / 6.0f);
-  return L.wall_mode == LBM_WALL_BSR ? 1.0f / (1.0f + X) : 2.0f - 2.0f / (1.0f + X);
+  const float X0 = cm * sqrtf(kPi * mx / 6.0f) * (L.r_form == LBM_R_SECOND ? sqrtf(mx) : 1.0f);
+  float r[2];
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    const float X = L.r_form == LBM_R_FIRST ? X0 : X0 * L.rsqrt_mh[sp];
+    r[sp] = L.wall_mode == LBM_WALL_BSR ? 1.0f / (1.0f + X) : 2.0f - 2.0f / (1.0f + X);
+  }
+  return make_float2(r[0], r[1]);
 }
 
 // Density-correction factors of Eq. rho2 for the ghost columns, from the
@@ -684,7 +704,7 @@ __device__ __forceinline__ bool interior(const Lat& L, int x) {
 
 // Per-CTA wall data for the strip: r (both walls), 1/tau_q (both walls).
 struct WallSmem {
-  float r[2][TX];
+  float2 r[2][TX];  // (species a, species b) per wall and column
   float om_q[2][TX];
 };
 
@@ -710,14 +730,16 @@ __device__ __forceinline__ void wall_prologue(const Lat& L, const ST* __restrict
     const bool needed = tq ? (wall == 0 ? j_begin < half : j_end > half)
                            : (wall == 0 ? j_begin == 0 : j_end == L.N);
     float v = 1.0f;
+    float2 rv = make_float2(1.0f, 1.0f);
     if (needed && interior(L, x)) {
       const int jw = wall == 0 ? 0 : L.N - 1;
       const float al = alpha[wall * L.Nx + x];
       if (!tq) {
-        v = dbb_r(L, C, fin, x, jw, al);
+        rv = dbb_r(L, C, fin, x, jw, al);
       } else {
         float fs[2][9];
-        const float rr = L.wall_mode == LBM_WALL_BSR ? dbb_r(L, C, fin, x, jw, al) : 0.0f;
+        const float2 rr = L.wall_mode == LBM_WALL_BSR ? dbb_r(L, C, fin, x, jw, al)
+                                                      : make_float2(0.0f, 0.0f);
         pull_node(fin, L, E, C, x, jw, rr, rr, fs);
         Macro m;
         macro(L, C, fs, m);
@@ -727,7 +749,7 @@ __device__ __forceinline__ void wall_prologue(const Lat& L, const ST* __restrict
     if (tq)
       sm.om_q[wall][tx] = v;
     else
-      sm.r[wall][tx] = v;
+      sm.r[wall][tx] = rv;
   }
   __syncthreads();
 }
@@ -1000,7 +1022,7 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
   if (xp >= L.Nx) xp -= L.Nx;
   const unsigned base = blockIdx.x * L.SS + 2 * tx;  // row 0, i = 0, species a of column x
   const int offl = (int)(idx(L, 0, 0, 0, xm) - base), offr = (int)(idx(L, 0, 0, 0, xp) - base);
-  const float r_bot = wsm.r[0][tx], r_top = wsm.r[1][tx];
+  const float2 r_bot = wsm.r[0][tx], r_top = wsm.r[1][tx];
   const int half = (L.N + 1) / 2;  // rows j < half (1-based 2J <= N+1) use the bottom tau_q
   KahanF acc[4];
   const bool reduce = DIAG || edge_strip;
@@ -1354,6 +1376,10 @@ int validate(const lbm_mix_params* p, int* Nx_out) {
   if (p->x_periodic != 0 && p->x_periodic != 1) return set_err(LBM_EINVAL, "x_periodic is 0 or 1");
   if (p->diag_every < 1) return set_err(LBM_EINVAL, "diag_every must be >= 1");
   if (p->reref_every < -1) return set_err(LBM_EINVAL, "reref_every must be >= -1");
+  if (p->r_form != LBM_R_FIRST && p->r_form != LBM_R_SPECIES && p->r_form != LBM_R_SECOND)
+    return set_err(LBM_EINVAL, "r_form must be LBM_R_FIRST, LBM_R_SPECIES or LBM_R_SECOND");
+  if (p->lambda_pressure != 0 && p->lambda_pressure != 1)
+    return set_err(LBM_EINVAL, "lambda_pressure must be 0 (partial) or 1 (mixture)");
   if (p->wall != LBM_WALL_DBB && p->wall != LBM_WALL_BSR)
     return set_err(LBM_EINVAL, "wall must be LBM_WALL_DBB or LBM_WALL_BSR");
   if (p->rounding != LBM_ROUND_STOCHASTIC && p->rounding != LBM_ROUND_NEAREST)
@@ -1378,6 +1404,8 @@ Lat derive(const lbm_mix_params* p, int Nx) {
   L.SS = (unsigned)((long)L.N * RS);
   L.x_periodic = p->x_periodic;
   L.wall_mode = p->wall;
+  L.r_form = p->r_form;
+  L.lam_mix = p->lambda_pressure;
   double m_min = fmin(p->m_a, p->m_b);
   double mh[2] = {p->m_a / m_min, p->m_b / m_min};
   L.light = (p->m_a <= p->m_b) ? 0 : 1;
@@ -1417,6 +1445,7 @@ Lat derive(const lbm_mix_params* p, int Nx) {
       (&L.kp2[k].x)[sp] = L.kp[sp][k];
     }
     L.mh[sp] = mh[sp];
+    L.rsqrt_mh[sp] = (float)(1.0 / sqrt(mh[sp]));
     double cxl = 3.0 * mu_s[sp] * sqrt(PI / (6.0 * mh[sp]));
     L.c_xl[sp] = (float)cxl;
     L.inv_c_xl[sp] = (float)(1.0 / cxl);

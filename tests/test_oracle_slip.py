@@ -120,9 +120,9 @@ def test_discrete_slip_closed_form_against_direct_solve(wall):
 
 
 def _steady(orc, N, Kn, alpha, c_m0, psi_off, L_over_H=6.0, theta=1.001, tol=1e-12,
-            wall_mode=0):
+            wall=0):
     p = dict(m_a=2.0, m_b=2.0, C_l=0.4, theta=theta, Kn_out=Kn, N=N, L_over_H=L_over_H,
-             accommodation=alpha, c_m0=c_m0, psi_off=psi_off, wall=wall_mode)
+             accommodation=alpha, c_m0=c_m0, psi_off=psi_off, wall=wall)
     o = orc.Oracle(p)
     o.init()
     prev = None
@@ -186,7 +186,7 @@ def test_single_gas_poiseuille_slip_bsr_wall(orc, N, Kn, alpha, c_m0):
     the factor of Eq. R, and tau_q of Eq. taoq realises the second-order slip
     solution exactly (measured to 3e-7, the pressure ratio's nonlinearity):
         G/(2 mu) y (H - y) + c_m lambda G H/(2 mu) + A_2 lambda^2 G/mu."""
-    u, G, lam, mu, rho = _steady(orc, N, Kn, alpha, c_m0, psi_off=1, wall_mode=1)
+    u, G, lam, mu, rho = _steady(orc, N, Kn, alpha, c_m0, psi_off=1, wall=1)
     A1, A2 = _A(alpha)
     c_m = c_m0 * (2 - alpha) / alpha
     y = np.arange(N) + 0.5

@@ -1,12 +1,17 @@
 """GPU parity: the sm_103a fused step (through the C ABI) against the FP64
 oracle, element by element, on the same seeded inputs.
 
-Tolerances (FP32 storage and arithmetic against FP64): densities to 1e-5 of
-their maximum, species velocities to RTOL_U of their maximum, scalar
-diagnostics as stated per test.  See the tolerance derivation in the design
-notes: one FP32 rounding of a population is ~6e-8 of the density; the
-velocity is a difference of populations ~30x smaller than the density, and
-errors accumulate over the relaxation time of the channel.
+Tolerances (FP32 storage and arithmetic against FP64), the relative 1e-5 on
+moments throughout: densities to 1e-5 of their maximum, species velocities
+to 1e-5 of the largest |u_x| (a velocity field has zeros, so its scale is
+its maximum), species mass flows to 1e-5 relative.  The floor they sit on
+was measured with the oracle itself storing its post-collision deviations
+in FP32 every step (its storage emulation): on the He-Ar 320 x 16 channel
+after 20 000 steps that alone moves rho by 1.3e-6, u_x by 2.5e-6, u_y by
+8.8e-7 and CL by 1.8e-6 absolute, and the GPU differs from the exact oracle
+by 1.5e-6, 3.9e-6, 9.8e-7 and 2.1e-6.  CL = (C_in - C_min)/C_in divides a
+difference of nearly equal mole fractions by C_in, so its floor is 1e-4
+relative for CL ~ 0.02; it is held to 1e-3 relative.
 """
 import numpy as np
 import pytest
@@ -17,7 +22,7 @@ from paper_1603_08221_gb300 import binding, workloads
 pytestmark = pytest.mark.gpu
 
 RTOL_RHO = 1e-5
-RTOL_U = 1e-4
+RTOL_U = 1e-5
 # Absolute floor for velocities: one FP32 rounding of a population is at most
 # 2^-24 of it and the rest population carries < 1/2 of rho, so u = sum c f / rho
 # is resolved to ~3e-8 by FP32 storage whatever its size.
@@ -369,5 +374,21 @@ def test_bsr_wall(N, Nx, steps, x_periodic):
     fp_g = g.get_post_state_f64()[..., 1:-1]
     fp_o = o.get_post_state()[..., 1:-1]
     assert _relerr(fp_g, fp_o) < RTOL_RHO
+    sg, so = g.separation(), o.separation()
+    assert abs(sg["CL"] - so["CL"]) < 1e-3 * max(abs(so["CL"]), 1e-4)
+
+
+@pytest.mark.parametrize("reading", [dict(r_form=binding.LBM_R_SPECIES),
+                                     dict(r_form=binding.LBM_R_SECOND, c_m0=0.6),
+                                     dict(lambda_pressure=1),
+                                     dict(r_form=binding.LBM_R_SPECIES, lambda_pressure=1,
+                                          wall=binding.LBM_WALL_BSR)])
+def test_alternative_readings(reading):
+    """The readings of Eq. R (species forms of r) and of lambda_sigma (with
+    the mixture pressure) against the oracle's same readings, on a channel
+    of unequal masses (He-Ar) where they differ from the defaults."""
+    p = workloads.preset("heli_argon_320x16", N=12, N_x=70, theta=1.5, **reading)
+    g, o = _pair(p, 200)
+    _check_moments(g, o)
     sg, so = g.separation(), o.separation()
     assert abs(sg["CL"] - so["CL"]) < 1e-3 * max(abs(so["CL"]), 1e-4)

@@ -16,7 +16,7 @@ from paper_1603_08221_gb300 import binding, workloads
 pytestmark = pytest.mark.gpu
 
 RTOL_RHO = 1e-5
-RTOL_U = 1e-4
+RTOL_U = 1e-5
 ATOL_U = 3e-8
 RTOL_SCHED = 1e-6
 
