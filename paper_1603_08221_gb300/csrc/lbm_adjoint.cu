@@ -61,34 +61,177 @@ struct AL {
 };
 
 // ------------------------------------------------ special functions (FP64)
-// 1/k for the series below (multiplications instead of FP64 divisions).
-__constant__ double kInvK[64] = {
-         0.0,  1.0 / 1,  1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,  1.0 / 7,
-     1.0 / 8,  1.0 / 9, 1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15,
-    1.0 / 16, 1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20, 1.0 / 21, 1.0 / 22, 1.0 / 23,
-    1.0 / 24, 1.0 / 25, 1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29, 1.0 / 30, 1.0 / 31,
-    1.0 / 32, 1.0 / 33, 1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39,
-    1.0 / 40, 1.0 / 41, 1.0 / 42, 1.0 / 43, 1.0 / 44, 1.0 / 45, 1.0 / 46, 1.0 / 47,
-    1.0 / 48, 1.0 / 49, 1.0 / 50, 1.0 / 51, 1.0 / 52, 1.0 / 53, 1.0 / 54, 1.0 / 55,
-    1.0 / 56, 1.0 / 57, 1.0 / 58, 1.0 / 59, 1.0 / 60, 1.0 / 61, 1.0 / 62, 1.0 / 63};
+// E_1 = E_i of Eq. psi in FP64, the FP64 pipe being the bound of the adjoint
+// kernels (six E_1 per node per step).  0 < x <= 1: the convergent series
+// (Abramowitz & Stegun 5.1.11) with a fixed number of terms (remainder
+// below 1e-20) by Horner's rule; 1 < x <= 32: R(x) = x e^x E_1(x), smooth
+// and between 0.59 and 0.97, as a Chebyshev series on [1,2], [2,4], [4,8],
+// [8,16], [16,32] (interpolants of R fitted in 40-digit arithmetic by
+// gen_e1_table.py, relative error below 2e-16), summed by Clenshaw's
+// recurrence; x > 32: the continued fraction (A&S 5.1.22, modified Lentz,
+// a handful of terms there).  No loop but the last has a data-dependent
+// length.
+// BEGIN generated E_1 tables (gen_e1_table.py)
+constexpr int kE1SeriesTerms = 20;
+__constant__ double kE1Series[kE1SeriesTerms] = {  // (-1)^k / (k k!), k = 1..
+    -1.0,
+    0.25,
+    -0.055555555555555555556,
+    0.010416666666666666667,
+    -0.0016666666666666666667,
+    0.00023148148148148148148,
+    -0.000028344671201814058957,
+    3.1001984126984126984e-6,
+    -3.061924358220654517e-7,
+    2.7557319223985890653e-8,
+    -2.2774643986765198886e-9,
+    1.7397297489890082483e-10,
+    -1.2353110643708934307e-11,
+    8.1933897126640890813e-13,
+    -5.0981091545465443173e-14,
+    2.9871733327421158109e-15,
+    -1.6537983849091298607e-16,
+    8.6773372047701258123e-18,
+    -4.3266501298022787984e-19,
+    2.0551588116560824292e-20};
+constexpr int kE1ChebTerms = 20;
+__constant__ double kE1Cheb[5][kE1ChebTerms] = {  // x e^x E_1(x) on [1,2] .. [16,32]
+    {  // [1, 2], max relative error 1.5e-16
+     0.66602904785893381259,
+     0.062425288438637690354,
+     -0.0064399715225844760029,
+     0.00071881049652994166717,
+     -0.000085371489910101236718,
+     0.000010648380975570467222,
+     -1.3809135417546289139e-6,
+     1.8477934175040391861e-7,
+     -2.5364639654694246794e-8,
+     3.5560115645720432054e-9,
+     -5.0741153091797847352e-10,
+     7.3492752014463539301e-11,
+     -1.078152203046921324e-11,
+     1.5992380399775897593e-12,
+     -2.3951298013872688691e-13,
+     3.6176510021764167969e-14,
+     -5.5082552205829415582e-15,
+     8.6349750770716804233e-16,
+     -1.2997392722785466931e-16,
+     0.0},
+    {  // [2, 4], max relative error 1.4e-16
+     0.78023590097585564412,
+     0.050579111577321273969,
+     -0.0061138064664468708916,
+     0.00076986586051874297637,
+     -0.00010029543689856821373,
+     0.000013441723236134673213,
+     -1.8447925285347978064e-6,
+     2.5831692135853972289e-7,
+     -3.6793586219991993821e-8,
+     5.318025436335566907e-9,
+     -7.784409115294749227e-10,
+     1.1520951705973502714e-10,
+     -1.721671160265668828e-11,
+     2.5948940888289542991e-12,
+     -3.9407860062066585244e-13,
+     6.0254449305202488572e-14,
+     -9.2692537700148199283e-15,
+     1.4346100679077652733e-15,
+     -2.283383004897064056e-16,
+     3.4804904108859155755e-17},
+    {  // [4, 8], max relative error 2.0e-16
+     0.86680483734339862145,
+     0.035729512355926419271,
+     -0.0048959245535215693208,
+     0.00068348200964272786034,
+     -0.000096976631812688221139,
+     0.000013956364689041613815,
+     -2.0337277146399378673e-6,
+     2.9963382373397474592e-7,
+     -4.4578239842876728156e-8,
+     6.6899752178875340627e-9,
+     -1.0118056680554136366e-9,
+     1.5409816786636522465e-10,
+     -2.3617216919622858371e-11,
+     3.6402643341138812429e-12,
+     -5.640079104779016553e-13,
+     8.7800007595891105482e-14,
+     -1.3735263486386159543e-14,
+     2.2082820530301247497e-15,
+     -3.3944047611846607383e-16,
+     0.0},
+    {  // [8, 16], max relative error 9.1e-17
+     0.92462581270744814032,
+     0.022426046904821617509,
+     -0.0033632854246972466529,
+     0.00050811207241193898218,
+     -0.000077277187286046253259,
+     0.000011824509210703231475,
+     -1.8193981013257861836e-6,
+     2.8137342677733913013e-7,
+     -4.3718887142567354835e-8,
+     6.8222087358153253457e-9,
+     -1.0688256661208552e-9,
+     1.6806821429678867679e-10,
+     -2.6518258872481906194e-11,
+     4.1974007458489564325e-12,
+     -6.663421095493081495e-13,
+     1.0607424373924901335e-13,
+     -1.6929635536870282355e-14,
+     2.7102415568166862627e-15,
+     -4.4552344095384109015e-16,
+     6.9784727943133395388e-17},
+    {  // [16, 32], max relative error 1.4e-16
+     0.95943546434241239268,
+     0.012870093055632837046,
+     -0.002047138091502517212,
+     0.00032643986998048115045,
+     -0.000052177796734008780111,
+     8.3586409027615562548e-6,
+     -1.3418329765298757476e-6,
+     2.1583592432992000242e-7,
+     -3.4782826071477127715e-8,
+     5.615373870172731813e-9,
+     -9.0808208397842418235e-10,
+     1.4708451362153951274e-10,
+     -2.3859953703679508441e-11,
+     3.8761522571891074711e-12,
+     -6.305660795720515857e-13,
+     1.0271434194219746467e-13,
+     -1.6752660181602291294e-14,
+     2.7374851966074719439e-15,
+     -4.5918922862569621225e-16,
+     7.3187533703321782192e-17},
+};
+// END generated E_1 tables
 
-// E_1 from its power series for x <= 8 (A&S 5.1.11; at most 45 terms, and
-// the series' cancellation leaves a relative error below 5e-10 at x = 8,
-// i.e. below 1.1e-12 absolute in psi = ... - x^2 E_1 and in psi') and its
-// continued fraction for x > 8 (A&S 5.1.22, modified Lentz, a dozen terms
-// there).  The series needs no FP64 division, the slow path of this part.
-// Both loops are bounded.
-__device__ double e1d(double x) {
-  if (x <= 8.0) {
-    double t = 1.0, s = 0.0;
-    for (int k = 1; k < 64; ++k) {
-      t *= -x * kInvK[k];
-      const double d = t * kInvK[k];
-      s += d;
-      if (fabs(d) < 1e-17 * fabs(s)) break;
-    }
-    return -kEulerGamma - log(x) - s;
+// sum_{k=1}^{K} (-x)^k / (k k!) by Horner's rule.
+__device__ __forceinline__ double e1_series_sum(double x) {
+  double s = kE1Series[kE1SeriesTerms - 1];
+  #pragma unroll
+  for (int k = kE1SeriesTerms - 2; k >= 0; --k) s = fma(s, x, kE1Series[k]);
+  return s * x;
+}
+
+// x e^x E_1(x) for 1 < x <= 32.
+__device__ __forceinline__ double e1_scaled(double x) {
+  int e;
+  frexp(x, &e);  // x = m 2^e, 1/2 <= m < 1: x in [2^(e-1), 2^e)
+  const int seg = min(max(e - 1, 0), 4);
+  const double lo = ldexp(1.0, seg), t = (x - lo) / lo * 2.0 - 1.0;  // [lo, 2 lo] -> [-1, 1]
+  const double* c = kE1Cheb[seg];
+  double b1 = 0.0, b2 = 0.0;
+  #pragma unroll
+  for (int k = kE1ChebTerms - 1; k >= 1; --k) {
+    const double b0 = fma(2.0 * t, b1, c[k] - b2);
+    b2 = b1;
+    b1 = b0;
   }
+  return fma(t, b1, c[0] - b2);
+}
+
+__device__ double e1d(double x) {
+  if (x <= 1.0) return -kEulerGamma - log(x) - e1_series_sum(x);
+  if (x <= 32.0) return e1_scaled(x) * exp(-x) / x;
   const double tiny = 1e-300;
   double b = x + 1.0, c = 1.0 / tiny, d = 1.0 / b, h = d;
   for (int i = 1; i < 200; ++i) {
@@ -105,6 +248,8 @@ __device__ double e1d(double x) {
 
 // psi(a) = 1 + (a - 1) e^{-a} - a^2 E_1(a) (Eq. psi), psi(0) = 0, and its
 // first two derivatives: psi' = 2 e^{-a} - 2 a E_1(a), psi'' = -2 E_1(a).
+// With R = a e^a E_1(a) for 1 < a <= 32: psi = 1 + e^{-a} ((a - 1) - a R),
+// psi' = 2 e^{-a} (1 - R), free of the cancellation in a^2 E_1.
 struct Psi3 {
   double v, d1, d2;
 };
@@ -116,7 +261,15 @@ __device__ Psi3 psid(double a) {
     p.d2 = -INFINITY;
     return p;
   }
-  const double e1 = e1d(a), ea = exp(-a);
+  const double ea = exp(-a);
+  if (a > 1.0 && a <= 32.0) {
+    const double R = e1_scaled(a);
+    p.v = fma(ea, (a - 1.0) - a * R, 1.0);
+    p.d1 = 2.0 * ea * (1.0 - R);
+    p.d2 = -2.0 * ea * R / a;
+    return p;
+  }
+  const double e1 = e1d(a);
   p.v = 1.0 + (a - 1.0) * ea - a * a * e1;
   p.d1 = 2.0 * ea - 2.0 * a * e1;
   p.d2 = -2.0 * e1;
