@@ -57,6 +57,7 @@ struct AL {
   int N, Nx, x_periodic, light;
   double s[2], mh[2], cw[2][3];  // rest weights w_i alpha_si: rest, axis, diagonal
   double c_lam, c_xl[2], c_ts, c_td, om_e, om_eps, c_m0, H;
+  double inv_c_lam, inv_c_xl[2];  // reciprocals (multiplications replace FP64 divisions)
   double rho_in[2], rho_out[2], C_in, C_out, theta;
 };
 
@@ -253,8 +254,10 @@ __device__ double e1d(double x) {
 struct Psi3 {
   double v, d1, d2;
 };
-__device__ Psi3 psid(double a) {
+template <bool D2 = false>
+__device__ __forceinline__ Psi3 psid(double a) {
   Psi3 p;
+  p.d2 = 0.0;
   if (!(a > 0.0)) {
     p.v = 0.0;
     p.d1 = 2.0;
@@ -266,13 +269,13 @@ __device__ Psi3 psid(double a) {
     const double R = e1_scaled(a);
     p.v = fma(ea, (a - 1.0) - a * R, 1.0);
     p.d1 = 2.0 * ea * (1.0 - R);
-    p.d2 = -2.0 * ea * R / a;
+    if (D2) p.d2 = -2.0 * ea * R / a;
     return p;
   }
   const double e1 = e1d(a);
   p.v = 1.0 + (a - 1.0) * ea - a * a * e1;
   p.d1 = 2.0 * ea - 2.0 * a * e1;
-  p.d2 = -2.0 * e1;
+  if (D2) p.d2 = -2.0 * e1;
   return p;
 }
 
@@ -356,6 +359,7 @@ __device__ void pull(const AL& L, const double* f, const double* r2, const doubl
 // Forward intermediates of one node, kept for the reverse pass.
 struct NodeFwd {
   double rho[2], jx[2], jy[2], rho_t, ux, uy, n, mx;
+  double inv_rho[2], inv_rt, inv_n, rs_mx, rs_xle[2];  // 1/rho_s, 1/rho, 1/n, m_x^-1/2, xle^-1/2
   double lam, Pm, dPm, tsm, om_s;     // mixture mean free path, Psi, dPsi/dlam, tau_s - 1/2, 1/tau_s
   double lams[2], Ps[2], dPs[2], xle[2], br, d, om_d;
   double m[2][9], meq[2][9];
@@ -378,14 +382,18 @@ __device__ __forceinline__ double Mki(int k, int i) {
     default: return cx * cy;
   }
 }
-__device__ __forceinline__ double Mnorm(int k) {
-  const double w[9] = {9.0, 36.0, 36.0, 6.0, 12.0, 6.0, 12.0, 4.0, 4.0};
+// 1 / |M_k|^2, the diagonal of (M M^T)^-1.
+__device__ __forceinline__ double inv_Mnorm(int k) {
+  const double w[9] = {1.0 / 9.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 6.0, 1.0 / 12.0,
+                       1.0 / 6.0, 1.0 / 12.0, 1.0 / 4.0, 1.0 / 4.0};
   return w[k];
 }
 
-__device__ double half_psi(double y, double H, double lam, double* dlam) {
-  const Psi3 a = psid(y / lam), b = psid((H - y) / lam);
-  if (dlam) *dlam = 0.5 * (a.d1 * (-y / (lam * lam)) + b.d1 * (-(H - y) / (lam * lam)));
+// Psi(y) = (psi(y/lambda) + psi((H-y)/lambda)) / 2 and dPsi/dlambda, from
+// 1/lambda.
+__device__ __forceinline__ double half_psi(double y, double H, double inv_lam, double* dlam) {
+  const Psi3 a = psid(y * inv_lam), b = psid((H - y) * inv_lam);
+  *dlam = -0.5 * (a.d1 * y + b.d1 * (H - y)) * inv_lam * inv_lam;
   return 0.5 * (a.v + b.v);
 }
 
@@ -408,21 +416,26 @@ __device__ void node_forward(const AL& L, const double g[2][9], double y, double
     F.jy[sp] = jy;
   }
   F.rho_t = F.rho[0] + F.rho[1];
-  F.ux = (F.jx[0] + F.jx[1]) / F.rho_t;
-  F.uy = (F.jy[0] + F.jy[1]) / F.rho_t;
+  F.inv_rt = 1.0 / F.rho_t;
+  F.ux = (F.jx[0] + F.jx[1]) * F.inv_rt;
+  F.uy = (F.jy[0] + F.jy[1]) * F.inv_rt;
   F.n = L.s[0] * F.rho[0] + L.s[1] * F.rho[1];
-  F.mx = F.rho_t / F.n;
-  F.lam = L.c_lam / (F.n * sqrt(F.mx));
-  F.Pm = half_psi(y, L.H, F.lam, &F.dPm);
-  F.tsm = F.lam * F.Pm * L.c_ts / sqrt(F.mx);
+  F.inv_n = 1.0 / F.n;
+  F.mx = F.rho_t * F.inv_n;
+  F.rs_mx = rsqrt(F.mx);
+  F.lam = L.c_lam * F.inv_n * F.rs_mx;
+  F.Pm = half_psi(y, L.H, F.n * F.mx * F.rs_mx * L.inv_c_lam, &F.dPm);
+  F.tsm = F.lam * F.Pm * L.c_ts * F.rs_mx;
   F.om_s = 1.0 / (0.5 + F.tsm);
   F.br = 0.0;
   #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
-    F.lams[sp] = L.c_xl[sp] / (L.s[sp] * F.rho[sp]);
-    F.Ps[sp] = half_psi(y, L.H, F.lams[sp], &F.dPs[sp]);
-    F.xle[sp] = L.c_xl[sp] * F.Ps[sp] / F.n;
-    F.br += 1.0 / sqrt(F.xle[sp]);
+    F.inv_rho[sp] = 1.0 / F.rho[sp];
+    F.lams[sp] = L.c_xl[sp] / L.s[sp] * F.inv_rho[sp];
+    F.Ps[sp] = half_psi(y, L.H, L.s[sp] * F.rho[sp] * L.inv_c_xl[sp], &F.dPs[sp]);
+    F.xle[sp] = L.c_xl[sp] * F.Ps[sp] * F.inv_n;
+    F.rs_xle[sp] = rsqrt(F.xle[sp]);
+    F.br += F.rs_xle[sp];
   }
   F.d = F.mx * F.br * F.br;
   F.om_d = F.d / (0.5 * F.d + L.c_td);
@@ -441,7 +454,7 @@ __device__ void node_forward(const AL& L, const double g[2][9], double y, double
       for (int i = 0; i < 9; ++i) mk += Mki(k, i) * g[sp][i];
       F.m[sp][k] = mk;
       F.meq[sp][k] = r * br[k];
-      dl[k] = S[k] * (mk - F.meq[sp][k]) / Mnorm(k);
+      dl[k] = S[k] * (mk - F.meq[sp][k]) * inv_Mnorm(k);
     }
     #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -479,7 +492,7 @@ __device__ void node_reverse(const AL& L, const double g[2][9], double y, double
       double dlb = 0;
       #pragma unroll
       for (int i = 0; i < 9; ++i) dlb -= Mki(k, i) * fbar[sp][i];
-      dlb /= Mnorm(k);
+      dlb *= inv_Mnorm(k);
       mbar[k] = S[k] * dlb;
       meqbar[k] = -S[k] * dlb;
       Sbar[k] += (F.m[sp][k] - F.meq[sp][k]) * dlb;
@@ -512,31 +525,33 @@ __device__ void node_reverse(const AL& L, const double g[2][9], double y, double
   const double brb = db * 2.0 * F.mx * F.br;
   #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
-    const double xleb = brb * (-0.5) / (F.xle[sp] * sqrt(F.xle[sp]));
+    const double rx = F.rs_xle[sp];
+    const double xleb = brb * (-0.5) * rx * rx * rx;
     // xle = c_xl Psi_s / n: proportional to mu through c_xl
-    const double Psb = xleb * L.c_xl[sp] / F.n;
-    nb -= xleb * F.xle[sp] / F.n;
+    const double Psb = xleb * L.c_xl[sp] * F.inv_n;
+    nb -= xleb * F.xle[sp] * F.inv_n;
     lnmub += xleb * F.xle[sp];
     const double lamsb = Psb * F.dPs[sp];
     // lam_s = c_xl / (s rho_s)
-    rhob[sp] -= lamsb * F.lams[sp] / F.rho[sp];
+    rhob[sp] -= lamsb * F.lams[sp] * F.inv_rho[sp];
     lnmub += lamsb * F.lams[sp];
   }
   // om_s = 1 / (1/2 + tsm); tsm = lam Psi(lam) c_ts m_x^{-1/2}
   const double tsmb = -omsb * F.om_s * F.om_s;
-  const double rsm = L.c_ts / sqrt(F.mx);
+  const double rsm = L.c_ts * F.rs_mx;
+  const double inv_mx = F.n * F.inv_rt;
   double lamb = tsmb * (F.Pm + F.lam * F.dPm) * rsm;
-  mxb += tsmb * F.tsm * (-0.5) / F.mx;
+  mxb += tsmb * F.tsm * (-0.5) * inv_mx;
   // lam = c_lam n^{-1} m_x^{-1/2}
-  nb -= lamb * F.lam / F.n;
-  mxb += lamb * F.lam * (-0.5) / F.mx;
+  nb -= lamb * F.lam * F.inv_n;
+  mxb += lamb * F.lam * (-0.5) * inv_mx;
   lnmub += lamb * F.lam;
   // m_x = rho / n; n = sum s rho_s
-  double rhotb = mxb / F.n;
-  nb -= mxb * F.rho_t / (F.n * F.n);
+  double rhotb = mxb * F.inv_n;
+  nb -= mxb * F.rho_t * F.inv_n * F.inv_n;
   // u = J / rho
-  rhotb -= (uxb * F.ux + uyb * F.uy) / F.rho_t;
-  const double Jxb = uxb / F.rho_t, Jyb = uyb / F.rho_t;
+  rhotb -= (uxb * F.ux + uyb * F.uy) * F.inv_rt;
+  const double Jxb = uxb * F.inv_rt, Jyb = uyb * F.inv_rt;
   #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     rhob[sp] += rhotb + nb * L.s[sp];
@@ -567,7 +582,7 @@ __device__ double tau_q(const AL& L, const double g[2][9], double alpha, double 
   const double lam = L.c_lam / (n * sqrt(mx));
   const double gg = L.c_ts / sqrt(mx);
   const double a = L.H / lam;
-  const Psi3 P = psid(a);
+  const Psi3 P = psid<true>(a);
   const double tt = 0.5 * lam * P.v * gg;
   const double dtt = 0.5 * gg * (2.0 - P.d1);
   const double A1 = (2.0 - alpha) / alpha * (1.0 - 0.1817 * alpha);
@@ -639,56 +654,51 @@ __device__ double block_sum256(double v, double* sm /* [8] */) {
 }
 
 // kappa of both ends (Eq. rho2) from the column sums of columns 1, 2 and
-// N_x - 2, N_x - 3 of f; one block.
+// N_x - 2, N_x - 3 of f; block e (of four) computes kappa[e], e = 2 end +
+// species.
 __global__ void __launch_bounds__(256) adj_kappa_kernel(AL L, const double* __restrict__ f,
                                                         double* __restrict__ kap) {
   __shared__ double sm[8];
-  const int t = threadIdx.x;
-  double acc[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  const int t = threadIdx.x, e = blockIdx.x, sp = e & 1;
+  const int x1 = e < 2 ? 1 : L.Nx - 2, x2 = e < 2 ? 2 : L.Nx - 3;
+  double a1 = 0.0, a2 = 0.0;
   if (!L.x_periodic) {
     for (int j = t; j < L.N; j += blockDim.x)
 #pragma unroll
-      for (int sp = 0; sp < 2; ++sp)
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          acc[sp][0] += f[fidx(L, sp, i, j, 1)];
-          acc[sp][1] += f[fidx(L, sp, i, j, 2)];
-          acc[2 + sp][0] += f[fidx(L, sp, i, j, L.Nx - 2)];
-          acc[2 + sp][1] += f[fidx(L, sp, i, j, L.Nx - 3)];
-        }
+      for (int i = 0; i < 9; ++i) {
+        a1 += f[fidx(L, sp, i, j, x1)];
+        a2 += f[fidx(L, sp, i, j, x2)];
+      }
   }
-  for (int e = 0; e < 4; ++e) {
-    // column sums enter as 2 c(1) - c(2) (resp. N_x - 2, N_x - 3)
-    const double D = block_sum256(2.0 * acc[e][0] - acc[e][1], sm);
-    if (t == 0) {
-      const double target = e < 2 ? L.rho_in[e] : L.rho_out[e - 2];
-      kap[e] = L.x_periodic ? 1.0 : L.N * target / D;
-    }
+  // column sums enter as 2 c(1) - c(2) (resp. N_x - 2, N_x - 3)
+  const double D = block_sum256(2.0 * a1 - a2, sm);
+  if (t == 0) {
+    const double target = e < 2 ? L.rho_in[sp] : L.rho_out[sp];
+    kap[e] = L.x_periodic ? 1.0 : L.N * target / D;
   }
 }
 
 // r of both walls and 1/tau_q of both halves per column.
+// r of wall w = blockIdx.y per column.
 __global__ void adj_cols_kernel(AL L, const double* __restrict__ f, const double* __restrict__ alpha,
                                 StepCols c) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, w = blockIdx.y;
   if (x >= L.Nx) return;
   if (!interior(L, x)) {
-    c.r[x] = c.r[L.Nx + x] = 0.0;
-    c.omq[x] = c.omq[L.Nx + x] = 1.0;
+    c.r[w * L.Nx + x] = 0.0;
+    c.omq[w * L.Nx + x] = 1.0;
     return;
   }
-  c.r[x] = dbb_r(L, f, x, 0, alpha[x], nullptr, nullptr);
-  c.r[L.Nx + x] = dbb_r(L, f, x, L.N - 1, alpha[L.Nx + x], nullptr, nullptr);
+  c.r[w * L.Nx + x] = dbb_r(L, f, x, w == 0 ? 0 : L.N - 1, alpha[w * L.Nx + x], nullptr, nullptr);
 }
+// 1/tau_q of the half of wall w = blockIdx.y per column.
 __global__ void adj_tauq_kernel(AL L, const double* __restrict__ f, const double* __restrict__ alpha,
                                 StepCols c) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, w = blockIdx.y;
   if (x >= L.Nx || !interior(L, x)) return;
-  for (int w = 0; w < 2; ++w) {
-    double g[2][9];
-    pull(L, f, c.r, c.kappa, x, w == 0 ? 0 : L.N - 1, g);
-    c.omq[w * L.Nx + x] = 1.0 / tau_q(L, g, alpha[w * L.Nx + x], 0.0, nullptr, nullptr, nullptr);
-  }
+  double g[2][9];
+  pull(L, f, c.r, c.kappa, x, w == 0 ? 0 : L.N - 1, g);
+  c.omq[w * L.Nx + x] = 1.0 / tau_q(L, g, alpha[w * L.Nx + x], 0.0, nullptr, nullptr, nullptr);
 }
 
 // One FP64 step over all nodes: f_out = Collide(Pull(f_in)).
@@ -826,30 +836,30 @@ __global__ void __launch_bounds__(128) adj_rev_node_kernel(
   }
 }
 
-// Reverse of tau_q per column and wall: adds to the wall nodes' gbar, the
-// accommodation adjoint and ln mu.  First sums the row-block partials of
-// adj_rev_node_kernel for this column in row-block order.
+// Reverse of tau_q per column and wall w = blockIdx.y: adds to the wall
+// nodes' gbar, the accommodation adjoint and ln mu (lnmu_col[w][x]).  First
+// sums the row-block partials of adj_rev_node_kernel for this column in
+// row-block order (the column's ln mu partials go to wall 0's slot).
 __global__ void adj_rev_tauq_kernel(AL L, const double* __restrict__ fin,
                                     const double* __restrict__ alpha, StepCols c,
                                     const double* __restrict__ part, int nparts,
                                     double* __restrict__ gbar, double* __restrict__ alphabar,
                                     double* __restrict__ lnmu_col) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, w = blockIdx.y;
   if (x >= L.Nx || !interior(L, x)) return;
-  double omqbar[2] = {0.0, 0.0}, lm = 0.0;
+  double omqbar = 0.0, lm = 0.0;
   for (int b = 0; b < nparts; ++b) {
     const double* pb = part + (size_t)b * 3 * L.Nx;
-    omqbar[0] += pb[x];
-    omqbar[1] += pb[L.Nx + x];
+    omqbar += pb[w * L.Nx + x];
     lm += pb[2 * L.Nx + x];
   }
-  lnmu_col[x] += lm;
-  for (int w = 0; w < 2; ++w) {
+  if (w == 0) lnmu_col[x] += lm;
+  {
     const int jw = w == 0 ? 0 : L.N - 1;
     double g[2][9], gb[2][9] = {};
     pull(L, fin, c.r, c.kappa, x, jw, g);
     const double omq = c.omq[w * L.Nx + x];
-    const double taub = -omqbar[w] * omq * omq;  // omq = 1/tau_q
+    const double taub = -omqbar * omq * omq;  // omq = 1/tau_q
     double ab = 0, lmb = 0;
     tau_q(L, g, alpha[w * L.Nx + x], taub, gb, &ab, &lmb);
     #pragma unroll
@@ -857,7 +867,7 @@ __global__ void adj_rev_tauq_kernel(AL L, const double* __restrict__ fin,
       #pragma unroll
       for (int i = 0; i < 9; ++i) gbar[fidx(L, sp, i, jw, x)] += gb[sp][i];
     alphabar[w * L.Nx + x] += ab;
-    lnmu_col[x] += lmb;
+    lnmu_col[w * L.Nx + x] += lmb;
   }
 }
 
@@ -939,59 +949,47 @@ __global__ void adj_rev_pull_kernel(AL L, const double* __restrict__ fin,
 
 // kappa adjoints (reduced over the end columns' rows), their terms in
 // lam_prev at columns 1, 2 and N_x - 2, N_x - 3, and the theta adjoint of
-// rho_in; one block, fixed order.
+// rho_in, fixed order.  Block e of a 4-block launch handles one (end,
+// species) pair e = 2 end + species; a 1-block launch handles all four in
+// turn (needed when N_x < 6, where the columns of the two ends overlap).
+// theta_acc[species] collects the inlet's theta adjoint.
 __global__ void __launch_bounds__(256) adj_rev_kappa_kernel(
     AL L, const double* __restrict__ fin, StepCols c, const double* __restrict__ gbar,
     double* __restrict__ lamp, double* __restrict__ theta_acc) {
   __shared__ double sm[8];
   const int t = threadIdx.x;
   if (L.x_periodic) return;
-  double acc[4] = {0, 0, 0, 0}, cs[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-  for (int jd = t; jd < L.N; jd += blockDim.x)
-#pragma unroll
-    for (int sp = 0; sp < 2; ++sp) {
+  const int e0 = gridDim.x == 4 ? blockIdx.x : 0, e1 = gridDim.x == 4 ? blockIdx.x + 1 : 4;
+  for (int e = e0; e < e1; ++e) {
+    const int sp = e & 1, inlet = e < 2;
+    const int x1 = inlet ? 1 : L.Nx - 2, x2 = inlet ? 2 : L.Nx - 3, dir = inlet ? 1 : -1;
+    double acc = 0.0, cs1 = 0.0, cs2 = 0.0;
+    for (int jd = t; jd < L.N; jd += blockDim.x) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
         const int js = jd - CYd[i];
-        if (js < 0 || js >= L.N) continue;
-        if (CXd[i] == 1)
-          acc[sp] += gbar[fidx(L, sp, i, jd, 1)] *
-                     (2.0 * fin[fidx(L, sp, i, js, 1)] - fin[fidx(L, sp, i, js, 2)]);
-        if (CXd[i] == -1)
-          acc[2 + sp] += gbar[fidx(L, sp, i, jd, L.Nx - 2)] *
-                         (2.0 * fin[fidx(L, sp, i, js, L.Nx - 2)] -
-                          fin[fidx(L, sp, i, js, L.Nx - 3)]);
-      }
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        cs[sp][0] += fin[fidx(L, sp, i, jd, 1)];
-        cs[sp][1] += fin[fidx(L, sp, i, jd, 2)];
-        cs[2 + sp][0] += fin[fidx(L, sp, i, jd, L.Nx - 2)];
-        cs[2 + sp][1] += fin[fidx(L, sp, i, jd, L.Nx - 3)];
+        if (CXd[i] == dir && js >= 0 && js < L.N)
+          acc += gbar[fidx(L, sp, i, jd, x1)] *
+                 (2.0 * fin[fidx(L, sp, i, js, x1)] - fin[fidx(L, sp, i, js, x2)]);
+        cs1 += fin[fidx(L, sp, i, jd, x1)];
+        cs2 += fin[fidx(L, sp, i, jd, x2)];
       }
     }
-  double kb[4], D[4];
-  for (int e = 0; e < 4; ++e) {
-    kb[e] = block_sum256(acc[e], sm);
-    D[e] = block_sum256(2.0 * cs[e][0] - cs[e][1], sm);
+    const double kb = block_sum256(acc, sm);
+    const double D = block_sum256(2.0 * cs1 - cs2, sm);
+    // kappa_in = N rho_in / D, rho_in,s = theta C_s m_s
+    if (inlet && t == 0) theta_acc[sp] += kb * c.kappa[e] / L.theta;
+    // d kappa / d f(x, j) = -kappa / D * (2 at column 1 (N_x-2), -1 at column 2 (N_x-3))
+    const double gk = -kb * c.kappa[e] / D;
+    for (int jd = t; jd < L.N; jd += blockDim.x) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        lamp[fidx(L, sp, i, jd, x1)] += 2.0 * gk;
+        lamp[fidx(L, sp, i, jd, x2)] -= gk;
+      }
+    }
+    __syncthreads();  // the next pair's columns may be this pair's (N_x < 6)
   }
-  // kappa_in = N rho_in / D, rho_in,s = theta C_s m_s
-  if (t == 0)
-    for (int sp = 0; sp < 2; ++sp) *theta_acc += kb[sp] * c.kappa[sp] / L.theta;
-  // d kappa / d f(x, j) = -kappa / D * (2 at column 1 (N_x-2), -1 at column 2 (N_x-3))
-  for (int jd = t; jd < L.N; jd += blockDim.x)
-#pragma unroll
-    for (int sp = 0; sp < 2; ++sp) {
-      const double gi = -kb[sp] * c.kappa[sp] / D[sp];
-      const double go = -kb[2 + sp] * c.kappa[2 + sp] / D[2 + sp];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        lamp[fidx(L, sp, i, jd, 1)] += 2.0 * gi;
-        lamp[fidx(L, sp, i, jd, 2)] -= gi;
-        lamp[fidx(L, sp, i, jd, L.Nx - 2)] += 2.0 * go;
-        lamp[fidx(L, sp, i, jd, L.Nx - 3)] -= go;
-      }
-    }
 }
 
 // sum over the state of a * b into one value per block (fixed order); the
@@ -1044,6 +1042,8 @@ AL derive_al(const lbm_mix_params* p, int Nx) {
     L.rho_out[sp] = Co[sp] * L.mh[sp];
   }
   L.c_lam = 3.0 * mu * sqrt(kPiD / 6.0);
+  L.inv_c_lam = 1.0 / L.c_lam;
+  for (int sp = 0; sp < 2; ++sp) L.inv_c_xl[sp] = 1.0 / L.c_xl[sp];
   L.c_ts = sqrt(6.0 / kPiD);
   L.c_td = 1.5 * sqrt(3.0 * (L.mh[0] + L.mh[1]) * L.mh[0] * L.mh[1]);
   L.om_e = 1.0 / p->tau_e;
@@ -1065,8 +1065,10 @@ struct lbm_adj {
   bool own_stream = false;
   size_t S = 0;      // doubles per state
   double* ckpt = nullptr;   // [ceil(T/K)+1][S] states at steps 0, K, 2K, ...
-  double* seg = nullptr;    // [K][S] replayed inputs of one segment's steps
-  double* segcols = nullptr;  // [K][4 Nx + 4] column data of those steps
+  double* seg[2] = {nullptr, nullptr};      // [K][S] replayed inputs of one segment's steps
+  double* segcols[2] = {nullptr, nullptr};  // [K][4 Nx + 4] column data of those steps
+  cudaStream_t rstream = nullptr;   // the replays of the backward sweep
+  cudaEvent_t ev_start = nullptr, ev_rep[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
   double* work[2] = {nullptr, nullptr};
   double* lam[2] = {nullptr, nullptr};
   double* gbar = nullptr;
@@ -1074,8 +1076,8 @@ struct lbm_adj {
   double* alpha = nullptr;    // [2][Nx]
   double* alphabar = nullptr;
   double* part_rev = nullptr;  // [ceil(N/REV_ROWS)][3][Nx] row-block partials
-  double* lnmu_col = nullptr; // [Nx]
-  double* theta_acc = nullptr;  // [1]
+  double* lnmu_col = nullptr; // [2][Nx] (per wall)
+  double* theta_acc = nullptr;  // [2] (per species)
   double* colsum = nullptr;   // [3][Nx]
   double* part = nullptr;     // [256]
   double* h_col = nullptr;    // host copy of colsum
@@ -1094,15 +1096,18 @@ StepCols cols_of(lbm_adj* a, double* base) {
   return c;
 }
 
-// Forward step from f (input) into fo, column data into cols.
-int fwd_step(lbm_adj* a, const double* f, double* fo, StepCols c) {
+// Forward step from f (input) into fo, column data into cols, on stream st.
+int fwd_step(lbm_adj* a, const double* f, double* fo, StepCols c, cudaStream_t st) {
   const AL& L = a->L;
-  adj_kappa_kernel<<<1, 256, 0, a->stream>>>(L, f, c.kappa);
+  adj_kappa_kernel<<<4, 256, 0, st>>>(L, f, c.kappa);
   const int cb = (L.Nx + 127) / 128;
-  adj_cols_kernel<<<cb, 128, 0, a->stream>>>(L, f, a->alpha, c);
-  adj_tauq_kernel<<<cb, 128, 0, a->stream>>>(L, f, a->alpha, c);
+  // one thread per (column, wall): small blocks spread the FP64 work of
+  // the wall columns over many SMs
+  const dim3 wg((L.Nx + 31) / 32, 2);
+  adj_cols_kernel<<<wg, 32, 0, st>>>(L, f, a->alpha, c);
+  adj_tauq_kernel<<<wg, 32, 0, st>>>(L, f, a->alpha, c);
   dim3 grd(cb, L.N);
-  adj_step_kernel<<<grd, 128, 0, a->stream>>>(L, f, fo, c);
+  adj_step_kernel<<<grd, 128, 0, st>>>(L, f, fo, c);
   CKA(cudaGetLastError());
   return LBM_OK;
 }
@@ -1175,8 +1180,16 @@ int lbm_adj_create(const lbm_mix_params* p, long nsteps, int checkpoint_every, v
 #define ALLOCA(ptr, bytes) \
   if (e == cudaSuccess) e = cudaMalloc((void**)&(ptr), (bytes))
   ALLOCA(a->ckpt, sizeof(double) * a->S * nck);
-  ALLOCA(a->seg, sizeof(double) * a->S * a->K);
-  ALLOCA(a->segcols, sizeof(double) * cw * a->K);
+  for (int b = 0; b < 2; ++b) {
+    ALLOCA(a->seg[b], sizeof(double) * a->S * a->K);
+    ALLOCA(a->segcols[b], sizeof(double) * cw * a->K);
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&a->rstream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a->ev_start, cudaEventDisableTiming);
+  for (int b = 0; b < 2; ++b) {
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a->ev_rep[b], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a->ev_rev[b], cudaEventDisableTiming);
+  }
   ALLOCA(a->work[0], sizeof(double) * a->S);
   ALLOCA(a->work[1], sizeof(double) * a->S);
   ALLOCA(a->lam[0], sizeof(double) * a->S);
@@ -1186,8 +1199,8 @@ int lbm_adj_create(const lbm_mix_params* p, long nsteps, int checkpoint_every, v
   ALLOCA(a->alpha, sizeof(double) * 2 * Nx);
   ALLOCA(a->alphabar, sizeof(double) * 2 * Nx);
   ALLOCA(a->part_rev, sizeof(double) * 3 * Nx * (size_t)((p->N + REV_ROWS - 1) / REV_ROWS));
-  ALLOCA(a->lnmu_col, sizeof(double) * Nx);
-  ALLOCA(a->theta_acc, sizeof(double));
+  ALLOCA(a->lnmu_col, sizeof(double) * 2 * Nx);
+  ALLOCA(a->theta_acc, sizeof(double) * 2);
   ALLOCA(a->colsum, sizeof(double) * 3 * Nx);
   ALLOCA(a->part, sizeof(double) * 256);
 #undef ALLOCA
@@ -1217,9 +1230,16 @@ int lbm_adj_create(const lbm_mix_params* p, long nsteps, int checkpoint_every, v
 void lbm_adj_destroy(lbm_adj* a) {
   if (!a) return;
   if (a->stream) cudaStreamSynchronize(a->stream);
+  if (a->rstream) cudaStreamSynchronize(a->rstream);
   cudaFree(a->ckpt);
-  cudaFree(a->seg);
-  cudaFree(a->segcols);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(a->seg[b]);
+    cudaFree(a->segcols[b]);
+    if (a->ev_rep[b]) cudaEventDestroy(a->ev_rep[b]);
+    if (a->ev_rev[b]) cudaEventDestroy(a->ev_rev[b]);
+  }
+  if (a->ev_start) cudaEventDestroy(a->ev_start);
+  if (a->rstream) cudaStreamDestroy(a->rstream);
   for (int k = 0; k < 2; ++k) {
     cudaFree(a->work[k]);
     cudaFree(a->lam[k]);
@@ -1259,7 +1279,7 @@ int lbm_adj_forward(lbm_adj* a, double* CL, double* flux) {
   const double* f = a->ckpt;
   for (long t = 1; t <= a->T; ++t) {
     double* fo = (t % a->K == 0) ? a->ckpt + a->S * (size_t)(t / a->K) : a->work[t & 1];
-    int st = fwd_step(a, f, fo, cols_of(a, a->segcols));
+    int st = fwd_step(a, f, fo, cols_of(a, a->segcols[0]), a->stream);
     if (st) return st;
     f = fo;
   }
@@ -1293,11 +1313,10 @@ int lbm_adj_gradient(lbm_adj* a, int objective, double* dtheta, double* dkn, dou
   if (dalpha && n_alpha != 2L * L.Nx)
     return lbm_internal_error(LBM_EINVAL, "dalpha needs 2 N_x = %d values", 2 * L.Nx);
   const dim3 grd((L.Nx + 127) / 128, L.N);
-  const int cb = (L.Nx + 127) / 128;
   const size_t cw = 4 * (size_t)L.Nx + 4;
   CKA(cudaMemsetAsync(a->alphabar, 0, sizeof(double) * 2 * L.Nx, a->stream));
-  CKA(cudaMemsetAsync(a->lnmu_col, 0, sizeof(double) * L.Nx, a->stream));
-  CKA(cudaMemsetAsync(a->theta_acc, 0, sizeof(double), a->stream));
+  CKA(cudaMemsetAsync(a->lnmu_col, 0, sizeof(double) * 2 * L.Nx, a->stream));
+  CKA(cudaMemsetAsync(a->theta_acc, 0, sizeof(double) * 2, a->stream));
   adj_seed_kernel<<<grd, 128, 0, a->stream>>>(L, objective, a->xstar, a->Sl, a->Sh, a->lam[0]);
   CKA(cudaGetLastError());
   int cur = 0;  // lam[cur] is the adjoint of the state after the step being reversed
@@ -1306,51 +1325,77 @@ int lbm_adj_gradient(lbm_adj* a, int objective, double* dtheta, double* dkn, dou
   // data are); it goes to the work buffer that does not hold f^T, so that
   // lbm_adj_state still returns the forward run's final state afterwards
   double* spare = a->work[1 - (a->T & 1)];
-  for (long sg = nseg - 1; sg >= 0; --sg) {
-    const long t0 = sg * a->K;  // segment replays steps t0+1 .. t1
-    const long t1 = (t0 + a->K < a->T) ? t0 + a->K : a->T;
-    // replay: inputs f^{t0} .. f^{t1-1} into seg, column data into segcols
-    CKA(cudaMemcpyAsync(a->seg, a->ckpt + a->S * (size_t)sg, sizeof(double) * a->S,
-                        cudaMemcpyDeviceToDevice, a->stream));
+  // Replay of segment sg (inputs f^{t0} .. f^{t1-1} and their column data)
+  // into buffer pair sg & 1, on the replay stream.
+  auto replay = [&](long sg) -> int {
+    const int b = (int)(sg & 1);
+    const long t0 = sg * a->K, t1 = (t0 + a->K < a->T) ? t0 + a->K : a->T;
+    CKA(cudaMemcpyAsync(a->seg[b], a->ckpt + a->S * (size_t)sg, sizeof(double) * a->S,
+                        cudaMemcpyDeviceToDevice, a->rstream));
     for (long t = t0 + 1; t <= t1; ++t) {
       const long k = t - t0 - 1;
-      double* fin = a->seg + a->S * (size_t)k;
-      double* fo = (t < t1) ? a->seg + a->S * (size_t)(k + 1) : spare;
-      int st = fwd_step(a, fin, fo, cols_of(a, a->segcols + cw * k));
+      double* fin = a->seg[b] + a->S * (size_t)k;
+      double* fo = (t < t1) ? a->seg[b] + a->S * (size_t)(k + 1) : spare;
+      int st = fwd_step(a, fin, fo, cols_of(a, a->segcols[b] + cw * k), a->rstream);
       if (st) return st;
     }
+    CKA(cudaEventRecord(a->ev_rep[b], a->rstream));
+    return LBM_OK;
+  };
+  // The replay of segment sg - 1 runs on the replay stream while segment
+  // sg is reversed on the handle's stream (double-buffered); a replay waits
+  // for the reverse that last used its buffer pair, a reverse for its
+  // replay.  Each kernel computes what it did in sequence, so the gradient
+  // is the same bit for bit.
+  CKA(cudaEventRecord(a->ev_start, a->stream));
+  CKA(cudaStreamWaitEvent(a->rstream, a->ev_start, 0));
+  int st0 = replay(nseg - 1);
+  if (st0) return st0;
+  for (long sg = nseg - 1; sg >= 0; --sg) {
+    const int b = (int)(sg & 1);
+    if (sg >= 1) {
+      if (sg + 1 <= nseg - 1) CKA(cudaStreamWaitEvent(a->rstream, a->ev_rev[(sg + 1) & 1], 0));
+      if ((st0 = replay(sg - 1))) return st0;
+    }
+    CKA(cudaStreamWaitEvent(a->stream, a->ev_rep[b], 0));
+    const long t0 = sg * a->K;
+    const long t1 = (t0 + a->K < a->T) ? t0 + a->K : a->T;
     for (long t = t1; t > t0; --t) {
       const long k = t - t0 - 1;
-      const double* fin = a->seg + a->S * (size_t)k;
-      StepCols c = cols_of(a, a->segcols + cw * k);
+      const double* fin = a->seg[b] + a->S * (size_t)k;
+      StepCols c = cols_of(a, a->segcols[b] + cw * k);
       const int nparts = (L.N + REV_ROWS - 1) / REV_ROWS;
       adj_rev_node_kernel<<<dim3((L.Nx + 31) / 32, nparts), dim3(32, 4), 0, a->stream>>>(
           L, fin, a->lam[cur], c, a->gbar, a->part_rev);
-      adj_rev_tauq_kernel<<<cb, 128, 0, a->stream>>>(L, fin, a->alpha, c, a->part_rev, nparts,
-                                                     a->gbar, a->alphabar, a->lnmu_col);
+      adj_rev_tauq_kernel<<<dim3((L.Nx + 31) / 32, 2), 32, 0, a->stream>>>(
+          L, fin, a->alpha, c, a->part_rev, nparts, a->gbar, a->alphabar, a->lnmu_col);
       adj_rev_pull_kernel<<<grd, 128, 0, a->stream>>>(L, fin, a->alpha, c, a->gbar,
                                                       a->lam[1 - cur], a->alphabar);
-      adj_rev_kappa_kernel<<<1, 256, 0, a->stream>>>(L, fin, c, a->gbar, a->lam[1 - cur],
-                                                      a->theta_acc);
+      // one block per (end, species) unless the end columns overlap
+      adj_rev_kappa_kernel<<<L.Nx >= 6 ? 4 : 1, 256, 0, a->stream>>>(
+          L, fin, c, a->gbar, a->lam[1 - cur], a->theta_acc);
       CKA(cudaGetLastError());
       cur = 1 - cur;
     }
+    CKA(cudaEventRecord(a->ev_rev[b], a->stream));
   }
   // theta through the initial state: lam^0 . d f^0 / d theta
   adj_dot_kernel<<<256, 256, 0, a->stream>>>(a->lam[cur], a->dtheta0, a->S, a->part);
   CKA(cudaGetLastError());
-  double* h = a->h_col;  // staging: [Nx] ln mu, [1] theta, [256] parts
-  CKA(cudaMemcpyAsync(h, a->lnmu_col, sizeof(double) * L.Nx, cudaMemcpyDeviceToHost, a->stream));
-  CKA(cudaMemcpyAsync(h + L.Nx, a->theta_acc, sizeof(double), cudaMemcpyDeviceToHost, a->stream));
-  CKA(cudaMemcpyAsync(h + L.Nx + 1, a->part, sizeof(double) * 256, cudaMemcpyDeviceToHost,
+  double* h = a->h_col;  // staging: [2][Nx] ln mu, [2] theta, [256] parts
+  CKA(cudaMemcpyAsync(h, a->lnmu_col, sizeof(double) * 2 * L.Nx, cudaMemcpyDeviceToHost,
+                      a->stream));
+  CKA(cudaMemcpyAsync(h + 2 * L.Nx, a->theta_acc, sizeof(double) * 2, cudaMemcpyDeviceToHost,
+                      a->stream));
+  CKA(cudaMemcpyAsync(h + 2 * L.Nx + 2, a->part, sizeof(double) * 256, cudaMemcpyDeviceToHost,
                       a->stream));
   if (dalpha)
     CKA(cudaMemcpyAsync(dalpha, a->alphabar, sizeof(double) * 2 * L.Nx, cudaMemcpyDeviceToHost,
                         a->stream));
   CKA(cudaStreamSynchronize(a->stream));
-  double lnmu = 0, th = h[L.Nx];
-  for (int x = 0; x < L.Nx; ++x) lnmu += h[x];
-  for (int k = 0; k < 256; ++k) th += h[L.Nx + 1 + k];
+  double lnmu = 0, th = h[2 * L.Nx] + h[2 * L.Nx + 1];
+  for (int x = 0; x < 2 * L.Nx; ++x) lnmu += h[x];
+  for (int k = 0; k < 256; ++k) th += h[2 * L.Nx + 2 + k];
   if (dtheta) *dtheta = th;
   if (dkn) *dkn = lnmu / a->p.Kn_out;  // mu is proportional to Kn_out
   return LBM_OK;

@@ -279,6 +279,20 @@ def test_helium_argon_320x16_20000_steps():
     assert sg["x_min"] == so["x_min"]
 
 
+def test_neon_argon_2048x32_2000_steps():
+    """The 1/16 linear-scale copy of the throughput workload (Ne-Ar, C_l =
+    0.3, theta = 3, Kn_out = 0.05, 2048 x 32) over 2000 steps: rho_s, u_s,
+    mass flows, C_l(x) and CL against the FP64 oracle."""
+    p = workloads.preset("neon_argon_2048x32")
+    g, o = _pair(p, 2000)
+    _check_moments(g, o)
+    sg, so = g.separation(), o.separation()
+    assert abs(sg["CL"] - so["CL"]) < 1e-6 + 1e-3 * abs(so["CL"])
+    assert np.abs(sg["Cl_profile"] - so["Cl_profile"]).max() < 1e-6
+    for k in ("mdot_a", "mdot_b"):
+        assert abs(sg[k] / so[k] - 1) < RTOL_U, k
+
+
 def test_neon_argon_full_size_one_step():
     """The 32768 x 512 throughput workload in the launch configuration the
     benchmark times: after 3 GPU steps, the oracle takes the GPU's
