@@ -400,8 +400,10 @@ typedef struct lbm_adj lbm_adj;
  * channel with its inlet and outlet, Eqs. rho1 and rho2, between DBB walls,
  * with the default readings) and allocates
  * the checkpoints (ceil(nsteps/checkpoint_every) + 1 states of 18 N N_x
- * doubles) and two intervals of replayed states (the backward sweep replays
- * one interval on a second, internal stream while it reverses the next).
+ * doubles) and two intervals of replayed states with 6 N N_x doubles of
+ * wall-confinement factors per step (the backward sweep replays one
+ * interval on a second, internal stream while it reverses the next, and the
+ * reverse reads the factors the replay evaluated).
  * stream: cudaStream_t or NULL for an own stream.  Errors: LBM_EINVAL,
  * LBM_ENOMEM, LBM_ECUDA. */
 int lbm_adj_create(const lbm_mix_params* p, long nsteps, int checkpoint_every, void* stream,

@@ -400,8 +400,12 @@ __device__ __forceinline__ double half_psi(double y, double H, double inv_lam, d
 // f_out = Collide(g): moments, relaxation rates (1/tau_s of Eq. taos,
 // 1/tau_d of Eq. EQFrsp, 1/tau_q from the wall), MRT relaxation
 // f' = g - M^{-1} S (m - m^eq).
+// psi_in (nullable): the node's Psi and dPsi/dlambda of the mixture and of
+// both species as an earlier node_forward stored them through psi_out
+// (nullable), six values `plane` doubles apart; read instead of evaluated.
 __device__ void node_forward(const AL& L, const double g[2][9], double y, double omq,
-                             NodeFwd& F, double fo[2][9]) {
+                             NodeFwd& F, double fo[2][9], const double* psi_in = nullptr,
+                             double* psi_out = nullptr, size_t plane = 0) {
   #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     double r = 0, jx = 0, jy = 0;
@@ -424,7 +428,12 @@ __device__ void node_forward(const AL& L, const double g[2][9], double y, double
   F.mx = F.rho_t * F.inv_n;
   F.rs_mx = rsqrt(F.mx);
   F.lam = L.c_lam * F.inv_n * F.rs_mx;
-  F.Pm = half_psi(y, L.H, F.n * F.mx * F.rs_mx * L.inv_c_lam, &F.dPm);
+  if (psi_in) {
+    F.Pm = psi_in[0];
+    F.dPm = psi_in[plane];
+  } else {
+    F.Pm = half_psi(y, L.H, F.n * F.mx * F.rs_mx * L.inv_c_lam, &F.dPm);
+  }
   F.tsm = F.lam * F.Pm * L.c_ts * F.rs_mx;
   F.om_s = 1.0 / (0.5 + F.tsm);
   F.br = 0.0;
@@ -432,10 +441,24 @@ __device__ void node_forward(const AL& L, const double g[2][9], double y, double
   for (int sp = 0; sp < 2; ++sp) {
     F.inv_rho[sp] = 1.0 / F.rho[sp];
     F.lams[sp] = L.c_xl[sp] / L.s[sp] * F.inv_rho[sp];
-    F.Ps[sp] = half_psi(y, L.H, L.s[sp] * F.rho[sp] * L.inv_c_xl[sp], &F.dPs[sp]);
+    if (psi_in) {
+      F.Ps[sp] = psi_in[(2 + 2 * sp) * plane];
+      F.dPs[sp] = psi_in[(3 + 2 * sp) * plane];
+    } else {
+      F.Ps[sp] = half_psi(y, L.H, L.s[sp] * F.rho[sp] * L.inv_c_xl[sp], &F.dPs[sp]);
+    }
     F.xle[sp] = L.c_xl[sp] * F.Ps[sp] * F.inv_n;
     F.rs_xle[sp] = rsqrt(F.xle[sp]);
     F.br += F.rs_xle[sp];
+  }
+  if (psi_out) {
+    psi_out[0] = F.Pm;
+    psi_out[plane] = F.dPm;
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+      psi_out[(2 + 2 * sp) * plane] = F.Ps[sp];
+      psi_out[(3 + 2 * sp) * plane] = F.dPs[sp];
+    }
   }
   F.d = F.mx * F.br * F.br;
   F.om_d = F.d / (0.5 * F.d + L.c_td);
@@ -471,10 +494,10 @@ __device__ void node_forward(const AL& L, const double g[2][9], double y, double
 // scales c_lam and c_xl).
 __device__ void node_reverse(const AL& L, const double g[2][9], double y, double omq,
                              const double fbar[2][9], double gbar[2][9], double* omq_bar,
-                             double* lnmu_bar) {
+                             double* lnmu_bar, const double* psi_in, size_t plane) {
   NodeFwd F;
   double fo[2][9];
-  node_forward(L, g, y, omq, F, fo);
+  node_forward(L, g, y, omq, F, fo, psi_in, nullptr, plane);
   const double S[9] = {0.0, L.om_e, L.om_eps, F.om_d, omq, F.om_d, omq, F.om_s, F.om_s};
   double Sbar[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   double rhob[2] = {0, 0}, jxb[2] = {0, 0}, jyb[2] = {0, 0};
@@ -702,8 +725,10 @@ __global__ void adj_tauq_kernel(AL L, const double* __restrict__ f, const double
 }
 
 // One FP64 step over all nodes: f_out = Collide(Pull(f_in)).
+// psi_out (nullable): [6][N][Nx] Psi values of this step for the reverse
+// sweep (see node_forward).
 __global__ void adj_step_kernel(AL L, const double* __restrict__ fin, double* __restrict__ fout,
-                                StepCols c) {
+                                StepCols c, double* __restrict__ psi_out) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (x >= L.Nx || !interior(L, x)) return;
@@ -712,7 +737,9 @@ __global__ void adj_step_kernel(AL L, const double* __restrict__ fin, double* __
   const int half = (L.N + 1) / 2;
   const double omq = c.omq[(j < half ? 0 : 1) * L.Nx + x];
   NodeFwd F;
-  node_forward(L, g, j + 0.5, omq, F, fo);
+  const size_t plane = (size_t)L.N * L.Nx;
+  node_forward(L, g, j + 0.5, omq, F, fo, nullptr,
+               psi_out ? psi_out + (size_t)j * L.Nx + x : nullptr, plane);
   #pragma unroll
   for (int sp = 0; sp < 2; ++sp)
     #pragma unroll
@@ -789,9 +816,10 @@ __global__ void adj_seed_kernel(AL L, int objective, int xs, double Sl, double S
 // within the block and written as per-row-block partials, which
 // adj_rev_tauq_kernel adds up in row-block order.
 constexpr int REV_ROWS = 8;
+// psi: [6][N][Nx] Psi values the replay of this step stored.
 __global__ void __launch_bounds__(128) adj_rev_node_kernel(
     AL L, const double* __restrict__ fin, const double* __restrict__ lam, StepCols c,
-    double* __restrict__ gbar, double* __restrict__ part) {
+    const double* __restrict__ psi, double* __restrict__ gbar, double* __restrict__ part) {
   __shared__ double red[3][4][32];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int x = blockIdx.x * 32 + tx;
@@ -809,7 +837,8 @@ __global__ void __launch_bounds__(128) adj_rev_node_kernel(
         for (int i = 0; i < 9; ++i) fb[sp][i] = lam[fidx(L, sp, i, j, x)];
       const int h = j < half ? 0 : 1;
       double oqb, lmb;
-      node_reverse(L, g, j + 0.5, c.omq[h * L.Nx + x], fb, gb, &oqb, &lmb);
+      node_reverse(L, g, j + 0.5, c.omq[h * L.Nx + x], fb, gb, &oqb, &lmb,
+                   psi + (size_t)j * L.Nx + x, (size_t)L.N * L.Nx);
 #pragma unroll
       for (int sp = 0; sp < 2; ++sp)
 #pragma unroll
@@ -1067,6 +1096,7 @@ struct lbm_adj {
   double* ckpt = nullptr;   // [ceil(T/K)+1][S] states at steps 0, K, 2K, ...
   double* seg[2] = {nullptr, nullptr};      // [K][S] replayed inputs of one segment's steps
   double* segcols[2] = {nullptr, nullptr};  // [K][4 Nx + 4] column data of those steps
+  double* segpsi[2] = {nullptr, nullptr};   // [K][6][N][Nx] Psi values of those steps
   cudaStream_t rstream = nullptr;   // the replays of the backward sweep
   cudaEvent_t ev_start = nullptr, ev_rep[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
   double* work[2] = {nullptr, nullptr};
@@ -1097,7 +1127,8 @@ StepCols cols_of(lbm_adj* a, double* base) {
 }
 
 // Forward step from f (input) into fo, column data into cols, on stream st.
-int fwd_step(lbm_adj* a, const double* f, double* fo, StepCols c, cudaStream_t st) {
+int fwd_step(lbm_adj* a, const double* f, double* fo, StepCols c, cudaStream_t st,
+             double* psi_out = nullptr) {
   const AL& L = a->L;
   adj_kappa_kernel<<<4, 256, 0, st>>>(L, f, c.kappa);
   const int cb = (L.Nx + 127) / 128;
@@ -1107,7 +1138,7 @@ int fwd_step(lbm_adj* a, const double* f, double* fo, StepCols c, cudaStream_t s
   adj_cols_kernel<<<wg, 32, 0, st>>>(L, f, a->alpha, c);
   adj_tauq_kernel<<<wg, 32, 0, st>>>(L, f, a->alpha, c);
   dim3 grd(cb, L.N);
-  adj_step_kernel<<<grd, 128, 0, st>>>(L, f, fo, c);
+  adj_step_kernel<<<grd, 128, 0, st>>>(L, f, fo, c, psi_out);
   CKA(cudaGetLastError());
   return LBM_OK;
 }
@@ -1183,6 +1214,7 @@ int lbm_adj_create(const lbm_mix_params* p, long nsteps, int checkpoint_every, v
   for (int b = 0; b < 2; ++b) {
     ALLOCA(a->seg[b], sizeof(double) * a->S * a->K);
     ALLOCA(a->segcols[b], sizeof(double) * cw * a->K);
+    ALLOCA(a->segpsi[b], sizeof(double) * 6 * (size_t)p->N * Nx * a->K);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&a->rstream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a->ev_start, cudaEventDisableTiming);
@@ -1235,6 +1267,7 @@ void lbm_adj_destroy(lbm_adj* a) {
   for (int b = 0; b < 2; ++b) {
     cudaFree(a->seg[b]);
     cudaFree(a->segcols[b]);
+    cudaFree(a->segpsi[b]);
     if (a->ev_rep[b]) cudaEventDestroy(a->ev_rep[b]);
     if (a->ev_rev[b]) cudaEventDestroy(a->ev_rev[b]);
   }
@@ -1325,8 +1358,9 @@ int lbm_adj_gradient(lbm_adj* a, int objective, double* dtheta, double* dkn, dou
   // data are); it goes to the work buffer that does not hold f^T, so that
   // lbm_adj_state still returns the forward run's final state afterwards
   double* spare = a->work[1 - (a->T & 1)];
-  // Replay of segment sg (inputs f^{t0} .. f^{t1-1} and their column data)
-  // into buffer pair sg & 1, on the replay stream.
+  // Replay of segment sg (inputs f^{t0} .. f^{t1-1}, their column data and
+  // Psi values) into buffer set sg & 1, on the replay stream.
+  const size_t psi_step = 6 * (size_t)L.N * L.Nx;
   auto replay = [&](long sg) -> int {
     const int b = (int)(sg & 1);
     const long t0 = sg * a->K, t1 = (t0 + a->K < a->T) ? t0 + a->K : a->T;
@@ -1336,7 +1370,8 @@ int lbm_adj_gradient(lbm_adj* a, int objective, double* dtheta, double* dkn, dou
       const long k = t - t0 - 1;
       double* fin = a->seg[b] + a->S * (size_t)k;
       double* fo = (t < t1) ? a->seg[b] + a->S * (size_t)(k + 1) : spare;
-      int st = fwd_step(a, fin, fo, cols_of(a, a->segcols[b] + cw * k), a->rstream);
+      int st = fwd_step(a, fin, fo, cols_of(a, a->segcols[b] + cw * k), a->rstream,
+                        a->segpsi[b] + psi_step * (size_t)k);
       if (st) return st;
     }
     CKA(cudaEventRecord(a->ev_rep[b], a->rstream));
@@ -1366,7 +1401,7 @@ int lbm_adj_gradient(lbm_adj* a, int objective, double* dtheta, double* dkn, dou
       StepCols c = cols_of(a, a->segcols[b] + cw * k);
       const int nparts = (L.N + REV_ROWS - 1) / REV_ROWS;
       adj_rev_node_kernel<<<dim3((L.Nx + 31) / 32, nparts), dim3(32, 4), 0, a->stream>>>(
-          L, fin, a->lam[cur], c, a->gbar, a->part_rev);
+          L, fin, a->lam[cur], c, a->segpsi[b] + psi_step * (size_t)k, a->gbar, a->part_rev);
       adj_rev_tauq_kernel<<<dim3((L.Nx + 31) / 32, 2), 32, 0, a->stream>>>(
           L, fin, a->alpha, c, a->part_rev, nparts, a->gbar, a->alphabar, a->lnmu_col);
       adj_rev_pull_kernel<<<grd, 128, 0, a->stream>>>(L, fin, a->alpha, c, a->gbar,

@@ -1,16 +1,35 @@
 """Reduced-precision storage (BF16 / FP16 deviations, FP32 arithmetic, FP64
-reductions) and re-referencing of the stored deviations.
+reductions) against the FP64 oracle, and re-referencing of the stored
+deviations.
 
-Re-referencing is exact arithmetic up to one rounding of the storage type, so
-with FP32 storage it is checked against the plain run at the parity
-tolerances.  BF16 and FP16 storage round every stored deviation to 8 or 11
-significant bits each step; their error against the FP32 run is bounded, not
-small.  The bounds below are the errors measured on this hardware for the
-Ne-Ar workload at 1/8 linear scale (2048 x 32, C_l = 0.5, theta = 2.5,
-Kn_out = 0.5) with the library's default re-referencing (every 256 steps),
-times two; the GPU path is deterministic (fixed-order reductions), so the
-measurement repeats exactly.
+The oracle references (tests/golden/lowp_*.txt, written by
+make_lowp_reference.py from the oracle alone) are on copies of the Ne-Ar
+reduced-precision workload (C_l = 0.5, theta = 2.5, Kn_out = 0.5, L/H = 64):
+the 1/8 linear-scale copy (2048 x 32) after 2000 and 20000 steps, and the
+1/16 copy (1024 x 16) at steady state (206 000 steps, residual 1e-9).
+
+Error model.  16-bit storage rounds every stored deviation each step;
+stochastic rounding (the default) makes each rounding error zero-mean and
+independent of the last, so the error of a run is one draw of a random
+process.  The oracle samples that process itself: run with its
+post-collision deviations rounded to the same format by stochastic rounding
+(its storage emulation, FP64 arithmetic otherwise), it differs from the
+exact oracle by the "model" errors the fixtures record (two generator
+seeds at 2000 steps, one otherwise).  The GPU's error is another draw of
+the same process, on top of its FP32 arithmetic.  One draw says little
+about a single quantity (at 20000 steps the one emulated BF16 run happens
+to move mdot_b by 8e-7 and mdot_a by 1.3e-4), so the model's scale is taken
+over the quantities one rounding process drives alike: the composition
+(CL, C~_l, C_l(x), absolute), the two mass flows (relative) and the six
+velocity profiles (relative to their columns' largest |u_x|).  Each
+quantity is held to K_MODEL times its group's largest emulated error plus
+the FP32 parity floor (1e-5 relative on velocities and mass flows, 1e-6
+absolute on mole fractions and CL).  Round to nearest has no such model: the same rounding repeats every
+step once the flow is steady and its bias accumulates; it is checked to be
+far worse than stochastic rounding.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -20,27 +39,102 @@ from paper_1603_08221_gb300 import binding, workloads
 pytestmark = pytest.mark.gpu
 
 RTOL_RHO = 1e-5
-RTOL_U = 1e-4
+RTOL_U = 1e-5
 ATOL_U = 3e-8
+K_MODEL = 3.0
+BF16_STEADY_CL = 0.10
+FLOOR = dict(CL=1e-6, Cl_tilde=1e-6, Cl_profile=1e-6, mdot=1e-5, u=1e-5)
 
-SCALE_1_8 = dict(N=32, N_x=2048)
-
-# measured error x 2 after 2000 steps, against the FP32 run
-BOUNDS_2000 = {
-    binding.LBM_BF16: dict(rho=5e-3, u=0.11, v=0.04, mdot=0.12, CL=3e-3),
-    binding.LBM_FP16: dict(rho=2e-3, u=0.025, v=6e-3, mdot=1e-3, CL=1e-3),
-}
-# steady state (residual 1e-8 or the step cap): CL relative, mass flow relative
-BOUNDS_STEADY = {
-    binding.LBM_BF16: dict(CL=0.30, mdot=0.08),
-    binding.LBM_FP16: dict(CL=0.30, mdot=0.01),
-}
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+STORAGE = {"bf16_sr": binding.LBM_BF16, "fp16_sr": binding.LBM_FP16}
 
 
 @pytest.fixture(scope="module", autouse=True)
 def _libs():
     binding.load()
     oracle.build()
+
+
+def _golden(name):
+    exact, model = {}, {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            w = line.split()
+            if w[0] == "exact":
+                exact[(int(w[1]), w[2])] = np.array([float(v) for v in w[3:]])
+            else:
+                model[(w[1], int(w[2]), int(w[3]), w[4])] = np.array([float(v) for v in w[5:]])
+    return exact, model
+
+
+def _params(N):
+    return dict(m_a=workloads.NE, m_b=workloads.AR, C_l=0.5, theta=2.5, Kn_out=0.5, N=N,
+                L_over_H=64.0)
+
+
+def _observe(g):
+    """The quantities the fixtures hold, from a GPU handle."""
+    s = g.separation()
+    m = g.moments()
+    nx = g.N_x
+    rec = {"CL": s["CL"], "Cl_tilde": s["Cl_tilde"], "mdot_a": s["mdot_a"],
+           "mdot_b": s["mdot_b"], "Cl_profile": s["Cl_profile"][::nx // 16]}
+    for f in (0.25, 0.5, 0.75):
+        x = int(f * nx)
+        rec[f"ua_x@{f}"] = m["ua_x"][:, x]
+        rec[f"ub_x@{f}"] = m["ub_x"][:, x]
+    return rec
+
+
+def _size(key, d, ref):
+    """Error measure of a difference d in quantity `key` (ref: exact
+    values): absolute for CL, C~_l and C_l(x); relative for the mass flows;
+    relative to the largest |u_x| of the column for velocities."""
+    d = np.abs(np.atleast_1d(d))
+    if key.startswith("mdot"):
+        return float(d.max() / abs(ref[0]))
+    if key.startswith("u"):
+        return float(d.max() / np.abs(ref).max())
+    return float(d.max())
+
+
+def _group(key):
+    if key.startswith("mdot"):
+        return "mdot"
+    if key.startswith("u"):
+        return "u"
+    return "composition"
+
+
+def _floor(key):
+    if key.startswith("mdot"):
+        return FLOOR["mdot"]
+    if key.startswith("u"):
+        return FLOOR["u"]
+    return FLOOR[key]
+
+
+def _check_against_model(fixture, N, steps_list, storage_name):
+    exact, model = _golden(fixture)
+    g = binding.LbmMix(storage=STORAGE[storage_name], **_params(N))
+    g.init()
+    done = 0
+    report = {}
+    for steps in steps_list:
+        g.step(steps - done)
+        done = steps
+        obs = _observe(g)
+        for key, val in obs.items():
+            ref = exact[(steps, key)]
+            err = _size(key, np.asarray(val) - ref, ref)
+            emul = max(_size(k, d, exact[(steps, k)]) for (st, _, h, k), d in model.items()
+                       if st == storage_name and h == steps and _group(k) == _group(key))
+            bound = K_MODEL * emul + _floor(key)
+            report[(steps, key)] = (err, emul)
+            assert err <= bound, (storage_name, steps, key, err, emul)
+    return report, exact
 
 
 def _relerr(a, b):
@@ -96,42 +190,37 @@ def test_rereference_against_oracle():
         assert np.abs(mg[k] - mo[k]).max() < RTOL_U * scale + ATOL_U, k
 
 
-@pytest.mark.parametrize("storage", [binding.LBM_BF16, binding.LBM_FP16])
-def test_reduced_precision_error_bounds_2000_steps(storage):
-    p = workloads.preset("neon_argon_16384x256", **SCALE_1_8)
-    ref = _run(p, 2000)
-    g = _run(p, 2000, storage=storage)
-    m, mr = g.moments(), ref.moments()
-    s, sr = g.separation(), ref.separation()
-    b = BOUNDS_2000[storage]
-    for k in ("rho_a", "rho_b"):
-        assert np.isfinite(m[k]).all()
-        assert _relerr(m[k], mr[k]) < b["rho"], (k, _relerr(m[k], mr[k]))
-    scale = max(np.abs(mr["ua_x"]).max(), np.abs(mr["ub_x"]).max())
-    for k in ("ua_x", "ub_x"):
-        assert np.abs(m[k] - mr[k]).max() < b["u"] * scale, k
-    for k in ("ua_y", "ub_y"):
-        assert np.abs(m[k] - mr[k]).max() < b["v"] * scale, k
-    for k in ("mdot_a", "mdot_b"):
-        assert abs(s[k] / sr[k] - 1) < b["mdot"], k
-    assert abs(s["CL"] - sr["CL"]) < b["CL"]
+@pytest.mark.parametrize("storage", ["bf16_sr", "fp16_sr"])
+def test_sixteen_bit_against_oracle_one_eighth_copy(storage):
+    """BF16 / FP16 storage with stochastic rounding on the 2048 x 32 copy
+    after 2000 and 20000 steps: CL, C~_l, mass flows, C_l(x) and the species
+    velocity profiles at three columns against the FP64 oracle, within the
+    error model."""
+    _check_against_model("lowp_neon_argon_2048x32.txt", 32, (2000, 20000), storage)
+
+
+@pytest.mark.parametrize("storage", ["bf16_sr", "fp16_sr"])
+def test_sixteen_bit_steady_state_against_oracle(storage):
+    """The 1024 x 16 copy at steady state (206 000 steps): every recorded
+    quantity within the error model, and CL within the stated bound of the
+    oracle's: 1 % for FP16, BF16_STEADY_CL for BF16."""
+    report, exact = _check_against_model("lowp_neon_argon_1024x16.txt", 16, (206000,), storage)
+    err, _ = report[(206000, "CL")]
+    cl = exact[(206000, "CL")][0]
+    assert err <= (0.01 if storage == "fp16_sr" else BF16_STEADY_CL) * cl, (err, cl)
 
 
 @pytest.mark.parametrize("storage", [binding.LBM_BF16, binding.LBM_FP16])
-def test_reduced_precision_steady_state(storage):
-    """Steady separation and mass flow of the 1/8-scale Ne-Ar channel against
-    the FP32 steady state (BF16 stalls at a residual near 1e-7: the rounding
-    noise floor, so its run stops at the step cap)."""
-    p = workloads.preset("neon_argon_16384x256", **SCALE_1_8)
-    ref = binding.LbmMix(**p)
-    ref.init()
-    assert ref.run_to_steady(1e-8, 400000, 1000)[0] == binding.LBM_OK
-    g = binding.LbmMix(storage=storage, **p)
-    g.init()
-    st, _, _ = g.run_to_steady(1e-8, 200000, 1000)
-    assert st in (binding.LBM_OK, binding.LBM_ENOTCONVERGED)
-    s, sr = g.separation(), ref.separation()
-    b = BOUNDS_STEADY[storage]
-    assert abs(s["CL"] / sr["CL"] - 1) < b["CL"]
-    for k in ("mdot_a", "mdot_b"):
-        assert abs(s[k] / sr[k] - 1) < b["mdot"], k
+def test_round_to_nearest_is_biased(storage):
+    """Round to nearest on the 2048 x 32 copy after 20000 steps: its CL
+    error against the oracle is more than ten times the error-model bound of
+    stochastic rounding (the repeated rounding of a steady flow acts like a
+    small body force on the momentum the collision conserves)."""
+    exact, model = _golden("lowp_neon_argon_2048x32.txt")
+    name = "bf16_sr" if storage == binding.LBM_BF16 else "fp16_sr"
+    g = _run(_params(32), 20000, storage=storage, rounding=binding.LBM_ROUND_NEAREST)
+    ref = exact[(20000, "CL")]
+    err = abs(g.separation()["CL"] - ref[0])
+    emul = max(abs(d[0]) for (st, _, h, k), d in model.items()
+               if st == name and h == 20000 and k == "CL")
+    assert err > 10 * (K_MODEL * emul + FLOOR["CL"]), (err, emul)
