@@ -400,10 +400,14 @@ typedef struct lbm_adj lbm_adj;
  * channel with its inlet and outlet, Eqs. rho1 and rho2, between DBB walls,
  * with the default readings) and allocates
  * the checkpoints (ceil(nsteps/checkpoint_every) + 1 states of 18 N N_x
- * doubles) and two intervals of replayed states with 6 N N_x doubles of
- * wall-confinement factors per step (the backward sweep replays one
- * interval on a second, internal stream while it reverses the next, and the
- * reverse reads the factors the replay evaluated).
+ * doubles) and two intervals of step inputs, each step with 6 N N_x doubles
+ * of wall-confinement factors and 4 N_x + 4 of column data (one interval
+ * when checkpoint_every >= nsteps).  The forward run keeps its last interval
+ * there; the backward sweep replays each other interval on a second,
+ * internal stream while it reverses the next, and the reverse reads the
+ * factors the forward run or the replay evaluated.  With
+ * checkpoint_every >= nsteps the forward run keeps every step (about
+ * 8 (24 N N_x + 4 N_x) bytes per step) and nothing is replayed.
  * stream: cudaStream_t or NULL for an own stream.  Errors: LBM_EINVAL,
  * LBM_ENOMEM, LBM_ECUDA. */
 int lbm_adj_create(const lbm_mix_params* p, long nsteps, int checkpoint_every, void* stream,
@@ -426,7 +430,9 @@ int lbm_adj_state(lbm_adj* a, double* f, long n);
 /* Backward sweep for `objective` after lbm_adj_forward: dJ/dtheta,
  * dJ/dKn_out and dJ/dalpha (host [2][N_x], n_alpha = 2 N_x); outputs
  * nullable.  theta enters the inlet densities (Eq. rho2) and the initial
- * state, Kn_out the viscosity that sets every mean free path. */
+ * state, Kn_out the viscosity that sets every mean free path.  May be
+ * called again after one forward run (either objective): every call gives
+ * what it gives after a fresh forward run, bit for bit. */
 int lbm_adj_gradient(lbm_adj* a, int objective, double* dtheta, double* dkn, double* dalpha,
                      long n_alpha);
 

@@ -49,8 +49,25 @@ namespace {
 
 constexpr double kPiD = 3.14159265358979323846;
 constexpr double kEulerGamma = 0.57721566490153286061;
-__constant__ int CXd[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-__constant__ int CYd[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+// D2Q9 velocities c_i = (cxd(i), cyd(i)) (Eq. c).  Compile-time functions,
+// not a table: in the unrolled loops the entries of M (Eq. m) and of the
+// momenta fold into the code, so the zero entries cost nothing and the unit
+// ones an add.
+__host__ __device__ constexpr int cxd(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cyd(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+// acc + c x for a coefficient c known at compile time: nothing for c = 0, an
+// add or a subtraction for c = +-1, one fma otherwise (for finite x the value
+// fma(c, x, acc) gives in every case; the compiler may not drop 0 x itself).
+__device__ __forceinline__ double macc(double acc, double c, double x) {
+  if (c == 0.0) return acc;
+  if (c == 1.0) return acc + x;
+  if (c == -1.0) return acc - x;
+  return fma(c, x, acc);
+}
 
 // FP64 lattice constants of one problem.
 struct AL {
@@ -299,7 +316,10 @@ struct StepCols {
   double* r;      // [2][Nx] bottom, top
   double* omq;    // [2][Nx]
   double* kappa;  // [4]: in_a, in_b, out_a, out_b
+  double* dq;     // [4][2][Nx]: d tau_q / d (rho_t, n, alpha, ln mu) per wall node
 };
+// doubles of one step's column data
+__host__ __device__ inline size_t cols_width(int Nx) { return 12 * (size_t)Nx + 4; }
 
 // ----------------------------------------------------------------- pull
 // Source value of population i of species sp at (xs, js): the stored state,
@@ -368,7 +388,7 @@ struct NodeFwd {
 // Rows of M in the order rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy
 // (Eq. m) and the diagonal of M M^T.
 __device__ __forceinline__ double Mki(int k, int i) {
-  const int cx = CXd[i], cy = CYd[i];
+  const int cx = cxd(i), cy = cyd(i);
   const int c2 = cx * cx + cy * cy;
   switch (k) {
     case 0: return 1.0;
@@ -412,8 +432,8 @@ __device__ void node_forward(const AL& L, const double g[2][9], double y, double
     #pragma unroll
     for (int i = 0; i < 9; ++i) {
       r += g[sp][i];
-      jx += CXd[i] * g[sp][i];
-      jy += CYd[i] * g[sp][i];
+      jx = macc(jx, cxd(i), g[sp][i]);
+      jy = macc(jy, cyd(i), g[sp][i]);
     }
     F.rho[sp] = r;
     F.jx[sp] = jx;
@@ -474,7 +494,7 @@ __device__ void node_forward(const AL& L, const double g[2][9], double y, double
     for (int k = 0; k < 9; ++k) {
       double mk = 0;
       #pragma unroll
-      for (int i = 0; i < 9; ++i) mk += Mki(k, i) * g[sp][i];
+      for (int i = 0; i < 9; ++i) mk = macc(mk, Mki(k, i), g[sp][i]);
       F.m[sp][k] = mk;
       F.meq[sp][k] = r * br[k];
       dl[k] = S[k] * (mk - F.meq[sp][k]) * inv_Mnorm(k);
@@ -483,7 +503,7 @@ __device__ void node_forward(const AL& L, const double g[2][9], double y, double
     for (int i = 0; i < 9; ++i) {
       double c = 0;
       #pragma unroll
-      for (int k = 0; k < 9; ++k) c += Mki(k, i) * dl[k];
+      for (int k = 0; k < 9; ++k) c = macc(c, Mki(k, i), dl[k]);
       fo[sp][i] = g[sp][i] - c;
     }
   }
@@ -514,7 +534,7 @@ __device__ void node_reverse(const AL& L, const double g[2][9], double y, double
     for (int k = 0; k < 9; ++k) {
       double dlb = 0;
       #pragma unroll
-      for (int i = 0; i < 9; ++i) dlb -= Mki(k, i) * fbar[sp][i];
+      for (int i = 0; i < 9; ++i) dlb = macc(dlb, -Mki(k, i), fbar[sp][i]);
       dlb *= inv_Mnorm(k);
       mbar[k] = S[k] * dlb;
       meqbar[k] = -S[k] * dlb;
@@ -524,7 +544,7 @@ __device__ void node_reverse(const AL& L, const double g[2][9], double y, double
     for (int i = 0; i < 9; ++i) {
       double c = 0;
       #pragma unroll
-      for (int k = 0; k < 9; ++k) c += Mki(k, i) * mbar[k];
+      for (int k = 0; k < 9; ++k) c = macc(c, Mki(k, i), mbar[k]);
       gbar[sp][i] += c;
     }
     // meq = rho_s (1, -4 + 2s + 3u^2, 4 - 3s - 3u^2, ux, -ux, uy, -uy, ux^2 - uy^2, ux uy)
@@ -581,59 +601,66 @@ __device__ void node_reverse(const AL& L, const double g[2][9], double y, double
     jxb[sp] += Jxb;
     jyb[sp] += Jyb;
     #pragma unroll
-    for (int i = 0; i < 9; ++i) gbar[sp][i] += rhob[sp] + CXd[i] * jxb[sp] + CYd[i] * jyb[sp];
+    for (int i = 0; i < 9; ++i)
+      gbar[sp][i] += macc(macc(rhob[sp], cxd(i), jxb[sp]), cyd(i), jyb[sp]);
   }
   *lnmu_bar = lnmub;
 }
 
 // --------------------------------------------------- wall quantities
-// tau_q of Eq. taoq from the pulled wall node (tau'_s(0) in its last term,
-// dx = 1) and the accommodation coefficient (Eq. A12).  With gbar != null
-// also the reverse: given taub = adjoint of tau_q, adds to gbar (the wall
-// node's pulled populations), *alphab and *lnmub.
-__device__ double tau_q(const AL& L, const double g[2][9], double alpha, double taub,
-                        double gbar[2][9], double* alphab, double* lnmub) {
+// Derivatives of tau_q with respect to its inputs (filled by tau_q_rho on
+// demand); the reverse of tau_q is these times the adjoint of tau_q.
+struct TauqBar {
+  double rt;     // rho_t = rho_a + rho_b: d/d g_i for every pulled population
+  double n;      // n = sum s rho_s: times s_sigma
+  double alpha;  // the accommodation coefficient
+  double lnmu;   // ln mu (c_lam is proportional to mu)
+};
+
+// tau_q of Eq. taoq from the densities of the pulled wall node (tau'_s(0) in
+// its last term, dx = 1) and the accommodation coefficient (Eq. A12); with
+// dq != null also its derivatives (reverse mode with a unit adjoint).
+// Three FP64 divisions (1/n, 1/tau'(0), 1/alpha); everything else
+// multiplies by them.
+__device__ double tau_q_rho(const AL& L, double rho0, double rho1, double alpha, TauqBar* dq) {
   const double vs = sqrt(kPiD / 6.0);
-  double rho[2];
-  #pragma unroll
-  for (int sp = 0; sp < 2; ++sp) {
-    rho[sp] = 0;
-    #pragma unroll
-    for (int i = 0; i < 9; ++i) rho[sp] += g[sp][i];
-  }
-  const double rt = rho[0] + rho[1], n = L.s[0] * rho[0] + L.s[1] * rho[1], mx = rt / n;
-  const double lam = L.c_lam / (n * sqrt(mx));
-  const double gg = L.c_ts / sqrt(mx);
-  const double a = L.H / lam;
+  const double rt = rho0 + rho1, n = L.s[0] * rho0 + L.s[1] * rho1;
+  const double inv_n = 1.0 / n;
+  const double mx = rt * inv_n;
+  const double rs = rsqrt(mx);                       // m_x^-1/2
+  const double lam = L.c_lam * inv_n * rs;           // mixture mean free path
+  const double inv_lam = n * mx * rs * L.inv_c_lam;
+  const double gg = L.c_ts * rs;
+  const double a = L.H * inv_lam;
   const Psi3 P = psid<true>(a);
   const double tt = 0.5 * lam * P.v * gg;
+  const double itt = 1.0 / tt;
+  const double i16 = 0.0625 * itt;                   // 1 / (16 tt)
   const double dtt = 0.5 * gg * (2.0 - P.d1);
-  const double A1 = (2.0 - alpha) / alpha * (1.0 - 0.1817 * alpha);
+  const double ial = 1.0 / alpha;
+  const double A1 = (2.0 - alpha) * ial * (1.0 - 0.1817 * alpha);
   const double A2 = 1.0 / kPiD + 0.5 * A1 * A1;
   const double Pn = 3.0 + 24.0 * vs * vs * tt * tt * A2;
   const double Qn = 12.0 + 30.0 * tt * vs * A1;
-  const double tq = 0.5 + Pn / (16.0 * tt) + dtt * Qn / (16.0 * tt * tt);
-  if (!gbar) return tq;
-  const double ttb = taub * (48.0 * vs * vs * tt * A2 / (16.0 * tt) - Pn / (16.0 * tt * tt) +
-                             dtt * 30.0 * vs * A1 / (16.0 * tt * tt) -
-                             2.0 * dtt * Qn / (16.0 * tt * tt * tt));
-  const double dttb = taub * Qn / (16.0 * tt * tt);
-  const double A2b = taub * 24.0 * vs * vs * tt * tt / (16.0 * tt);
-  const double A1b = taub * dtt * 30.0 * vs / (16.0 * tt) + A2b * A1;
-  *alphab += A1b * ((-2.0 / (alpha * alpha)) * (1.0 - 0.1817 * alpha) +
-                    (2.0 - alpha) / alpha * (-0.1817));
+  const double tq = 0.5 + Pn * i16 + dtt * Qn * i16 * itt;
+  if (!dq) return tq;
+  const double ttb = 48.0 * vs * vs * tt * A2 * i16 - Pn * i16 * itt +
+                     dtt * 30.0 * vs * A1 * i16 * itt - 2.0 * dtt * Qn * i16 * itt * itt;
+  const double dttb = Qn * i16 * itt;
+  const double A2b = 24.0 * vs * vs * tt * tt * i16;
+  const double A1b = dtt * 30.0 * vs * i16 + A2b * A1;
+  dq->alpha = A1b * ((-2.0 * ial * ial) * (1.0 - 0.1817 * alpha) + (2.0 - alpha) * ial * (-0.1817));
   // tt = lam psi(H/lam) gg / 2, dtt = gg (2 - psi'(H/lam)) / 2
-  double lamb = ttb * 0.5 * gg * (P.v - a * P.d1) + dttb * 0.5 * gg * P.d2 * a / lam;
-  double mxb = (ttb * tt + dttb * dtt) * (-0.5) / mx;
-  double nb = -lamb * lam / n;
-  mxb += lamb * lam * (-0.5) / mx;
-  *lnmub += lamb * lam;
-  const double rtb = mxb / n;
-  nb -= mxb * rt / (n * n);
-  #pragma unroll
-  for (int sp = 0; sp < 2; ++sp)
-    #pragma unroll
-    for (int i = 0; i < 9; ++i) gbar[sp][i] += rtb + nb * L.s[sp];
+  const double lamb = ttb * 0.5 * gg * (P.v - a * P.d1) + dttb * 0.5 * gg * P.d2 * a * inv_lam;
+  const double inv_mx = rs * rs;
+  double mxb = (ttb * tt + dttb * dtt) * (-0.5) * inv_mx;
+  double nb = -lamb * lam * inv_n;
+  mxb += lamb * lam * (-0.5) * inv_mx;
+  dq->lnmu = lamb * lam;
+  // m_x = rho_t / n
+  dq->rt = mxb * inv_n;
+  nb -= mxb * rt * inv_n * inv_n;
+  dq->n = nb;
   return tq;
 }
 
@@ -714,36 +741,58 @@ __global__ void adj_cols_kernel(AL L, const double* __restrict__ f, const double
   }
   c.r[w * L.Nx + x] = dbb_r(L, f, x, w == 0 ? 0 : L.N - 1, alpha[w * L.Nx + x], nullptr, nullptr);
 }
-// 1/tau_q of the half of wall w = blockIdx.y per column.
+// 1/tau_q of the half of wall w = blockIdx.y per column, and the
+// derivatives of tau_q the reverse sweep multiplies by the adjoint of tau_q
+// (c.dq).  One thread per (wall, column): the FP64 pipe takes a warp's 32
+// lanes at once, so a thread per wall node is the cheap layout.
 __global__ void adj_tauq_kernel(AL L, const double* __restrict__ f, const double* __restrict__ alpha,
                                 StepCols c) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, w = blockIdx.y;
   if (x >= L.Nx || !interior(L, x)) return;
   double g[2][9];
   pull(L, f, c.r, c.kappa, x, w == 0 ? 0 : L.N - 1, g);
-  c.omq[w * L.Nx + x] = 1.0 / tau_q(L, g, alpha[w * L.Nx + x], 0.0, nullptr, nullptr, nullptr);
+  double rho[2];
+  #pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    rho[sp] = 0;
+    #pragma unroll
+    for (int i = 0; i < 9; ++i) rho[sp] += g[sp][i];
+  }
+  TauqBar d;
+  const size_t k = (size_t)w * L.Nx + x, wn = 2 * (size_t)L.Nx;
+  c.omq[k] = 1.0 / tau_q_rho(L, rho[0], rho[1], alpha[k], &d);
+  c.dq[k] = d.rt;
+  c.dq[wn + k] = d.n;
+  c.dq[2 * wn + k] = d.alpha;
+  c.dq[3 * wn + k] = d.lnmu;
 }
 
-// One FP64 step over all nodes: f_out = Collide(Pull(f_in)).
+// One FP64 step over all nodes: f_out = Collide(Pull(f_in)).  One warp per
+// block, block (bx, by) covers 32 columns x `rows` rows (see node_rows).
 // psi_out (nullable): [6][N][Nx] Psi values of this step for the reverse
-// sweep (see node_forward).
-__global__ void adj_step_kernel(AL L, const double* __restrict__ fin, double* __restrict__ fout,
-                                StepCols c, double* __restrict__ psi_out) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y;
+// sweep (see node_forward).  At least 19 resident blocks per SM (ptxas then
+// keeps 96 registers and spills a few values to L1): 2888 blocks fit on 152
+// SMs, one row per block for the 2560 warps of a 1280 x 64 channel.
+__global__ void __launch_bounds__(32, 19) adj_step_kernel(AL L, const double* __restrict__ fin,
+                                                      double* __restrict__ fout, StepCols c,
+                                                      double* __restrict__ psi_out, int rows) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
   if (x >= L.Nx || !interior(L, x)) return;
-  double g[2][9], fo[2][9];
-  pull(L, fin, c.r, c.kappa, x, j, g);
+  const int j0 = blockIdx.y * rows, j1 = min(L.N, j0 + rows);
   const int half = (L.N + 1) / 2;
-  const double omq = c.omq[(j < half ? 0 : 1) * L.Nx + x];
-  NodeFwd F;
   const size_t plane = (size_t)L.N * L.Nx;
-  node_forward(L, g, j + 0.5, omq, F, fo, nullptr,
-               psi_out ? psi_out + (size_t)j * L.Nx + x : nullptr, plane);
-  #pragma unroll
-  for (int sp = 0; sp < 2; ++sp)
+  for (int j = j0; j < j1; ++j) {
+    double g[2][9], fo[2][9];
+    pull(L, fin, c.r, c.kappa, x, j, g);
+    const double omq = c.omq[(j < half ? 0 : 1) * L.Nx + x];
+    NodeFwd F;
+    node_forward(L, g, j + 0.5, omq, F, fo, nullptr,
+                 psi_out ? psi_out + (size_t)j * L.Nx + x : nullptr, plane);
     #pragma unroll
-    for (int i = 0; i < 9; ++i) fout[fidx(L, sp, i, j, x)] = fo[sp][i];
+    for (int sp = 0; sp < 2; ++sp)
+      #pragma unroll
+      for (int i = 0; i < 9; ++i) fout[fidx(L, sp, i, j, x)] = fo[sp][i];
+  }
 }
 
 // Initial state (rest equilibrium of the linear pressure and composition
@@ -779,7 +828,7 @@ __global__ void adj_colsum_kernel(AL L, const double* __restrict__ f, double* __
       const double a = f[fidx(L, L.light, i, j, x)], b = f[fidx(L, 1 - L.light, i, j, x)];
       nl += L.s[L.light] * a;
       nh += L.s[1 - L.light] * b;
-      jl += CXd[i] * a;
+      jl = macc(jl, cxd(i), a);
     }
   out[x] = nl;
   out[L.Nx + x] = nh;
@@ -804,111 +853,108 @@ __global__ void adj_seed_kernel(AL L, int objective, int xs, double Sl, double S
         const double dC = sp == L.light ? Sh / (Sn * Sn) : -Sl / (Sn * Sn);
         v = -dC * L.s[sp] / L.C_in;
       } else if (objective == 1 && x == L.Nx - 2 && sp == L.light) {
-        v = CXd[i];
+        v = cxd(i);
       }
       lam[fidx(L, sp, i, j, x)] = v;
     }
 }
 
-// Reverse of Collide for every node: gbar = (dCollide/dg)^T lam_t.  Block
-// (32, 4) covers 32 columns x REV_ROWS rows, so the grid spreads over all
-// SMs; the adjoints of 1/tau_q (per half) and of ln mu are summed per column
-// within the block and written as per-row-block partials, which
-// adj_rev_tauq_kernel adds up in row-block order.
-constexpr int REV_ROWS = 8;
-// psi: [6][N][Nx] Psi values the replay of this step stored.
-__global__ void __launch_bounds__(128) adj_rev_node_kernel(
+// Reverse of Collide for every node: gbar = (dCollide/dg)^T lam_t, and
+// per node the adjoints of 1/tau_q (of the node's half) and of ln mu,
+// stored per row for adj_rev_tauq_kernel to sum in row order:
+// part[j][0][x], part[j][1][x].  One warp per block, block (bx, by) covers
+// 32 columns x `rows` rows (see node_rows: every block fits on the GPU at
+// once, so the SMs share the work to within one block).
+// psi: [6][N][Nx] Psi values the forward run or the replay of this step
+// stored.
+__global__ void __launch_bounds__(32) adj_rev_node_kernel(
     AL L, const double* __restrict__ fin, const double* __restrict__ lam, StepCols c,
-    const double* __restrict__ psi, double* __restrict__ gbar, double* __restrict__ part) {
-  __shared__ double red[3][4][32];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x = blockIdx.x * 32 + tx;
-  const int j0 = blockIdx.y * REV_ROWS;
-  const int j1 = min(L.N, j0 + REV_ROWS);
+    const double* __restrict__ psi, int rows, double* __restrict__ gbar,
+    double* __restrict__ part) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  if (x >= L.Nx || !interior(L, x)) return;
+  const int j0 = blockIdx.y * rows, j1 = min(L.N, j0 + rows);
   const int half = (L.N + 1) / 2;
-  double accq[2] = {0, 0}, accm = 0;
-  if (x < L.Nx && interior(L, x)) {
-    for (int j = j0 + ty; j < j1; j += 4) {
-      double g[2][9], fb[2][9], gb[2][9];
-      pull(L, fin, c.r, c.kappa, x, j, g);
+  for (int j = j0; j < j1; ++j) {
+    double g[2][9], fb[2][9], gb[2][9];
+    pull(L, fin, c.r, c.kappa, x, j, g);
 #pragma unroll
-      for (int sp = 0; sp < 2; ++sp)
+    for (int sp = 0; sp < 2; ++sp)
 #pragma unroll
-        for (int i = 0; i < 9; ++i) fb[sp][i] = lam[fidx(L, sp, i, j, x)];
-      const int h = j < half ? 0 : 1;
-      double oqb, lmb;
-      node_reverse(L, g, j + 0.5, c.omq[h * L.Nx + x], fb, gb, &oqb, &lmb,
-                   psi + (size_t)j * L.Nx + x, (size_t)L.N * L.Nx);
+      for (int i = 0; i < 9; ++i) fb[sp][i] = lam[fidx(L, sp, i, j, x)];
+    const int h = j < half ? 0 : 1;
+    double oqb, lmb;
+    node_reverse(L, g, j + 0.5, c.omq[h * L.Nx + x], fb, gb, &oqb, &lmb,
+                 psi + (size_t)j * L.Nx + x, (size_t)L.N * L.Nx);
 #pragma unroll
-      for (int sp = 0; sp < 2; ++sp)
+    for (int sp = 0; sp < 2; ++sp)
 #pragma unroll
-        for (int i = 0; i < 9; ++i) gbar[fidx(L, sp, i, j, x)] = gb[sp][i];
-      accq[h] += oqb;
-      accm += lmb;
-    }
-  }
-  red[0][ty][tx] = accq[0];
-  red[1][ty][tx] = accq[1];
-  red[2][ty][tx] = accm;
-  __syncthreads();
-  if (ty == 0 && x < L.Nx) {
-    double a = 0, b = 0, m = 0;
-    for (int k = 0; k < 4; ++k) {
-      a += red[0][k][tx];
-      b += red[1][k][tx];
-      m += red[2][k][tx];
-    }
-    double* pb = part + (size_t)blockIdx.y * 3 * L.Nx;
-    pb[x] = a;
-    pb[L.Nx + x] = b;
-    pb[2 * L.Nx + x] = m;
+      for (int i = 0; i < 9; ++i) gbar[fidx(L, sp, i, j, x)] = gb[sp][i];
+    part[(size_t)(2 * j) * L.Nx + x] = oqb;
+    part[(size_t)(2 * j + 1) * L.Nx + x] = lmb;
   }
 }
 
-// Reverse of tau_q per column and wall w = blockIdx.y: adds to the wall
-// nodes' gbar, the accommodation adjoint and ln mu (lnmu_col[w][x]).  First
-// sums the row-block partials of adj_rev_node_kernel for this column in
-// row-block order (the column's ln mu partials go to wall 0's slot).
-__global__ void adj_rev_tauq_kernel(AL L, const double* __restrict__ fin,
-                                    const double* __restrict__ alpha, StepCols c,
-                                    const double* __restrict__ part, int nparts,
-                                    double* __restrict__ gbar, double* __restrict__ alphabar,
-                                    double* __restrict__ lnmu_col) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, w = blockIdx.y;
-  if (x >= L.Nx || !interior(L, x)) return;
+// Sum over the warp by a butterfly: every lane gets the same value (each
+// stage adds the same two operands in every lane).
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Reverse of tau_q per column and wall: one warp per (wall, column), item
+// = w N_x + x, kRevTauqWarps per block.  The lanes load the per-row partials
+// of adj_rev_node_kernel over the rows of wall w's half (lane-strided, so
+// the loads are in flight together) and sum them by a butterfly; then the
+// adjoint of tau_q times the derivatives the forward run stored (c.dq) goes
+// to the wall node's gbar (lanes 0..17, one population each), the
+// accommodation adjoint and ln mu (lnmu_col[w][x]).  The scalar work after
+// the sum is a dozen FP64 operations, so its repetition across the lanes
+// costs little.
+constexpr int kRevTauqWarps = 4;
+__global__ void __launch_bounds__(32 * kRevTauqWarps) adj_rev_tauq_kernel(
+    AL L, StepCols c, const double* __restrict__ part, double* __restrict__ gbar,
+    double* __restrict__ alphabar, double* __restrict__ lnmu_col) {
+  const int lane = threadIdx.x & 31;
+  const int item = blockIdx.x * kRevTauqWarps + (threadIdx.x >> 5);
+  if (item >= 2 * L.Nx) return;  // warp-uniform
+  const int w = item >= L.Nx ? 1 : 0, x = item - w * L.Nx;
+  if (!interior(L, x)) return;   // warp-uniform
+  const int half = (L.N + 1) / 2;
+  const int ja = w == 0 ? 0 : half, jb = w == 0 ? half : L.N;
   double omqbar = 0.0, lm = 0.0;
-  for (int b = 0; b < nparts; ++b) {
-    const double* pb = part + (size_t)b * 3 * L.Nx;
-    omqbar += pb[w * L.Nx + x];
-    lm += pb[2 * L.Nx + x];
+  for (int j = ja + lane; j < jb; j += 32) {
+    omqbar += part[(size_t)(2 * j) * L.Nx + x];
+    lm += part[(size_t)(2 * j + 1) * L.Nx + x];
   }
-  if (w == 0) lnmu_col[x] += lm;
-  {
+  omqbar = warp_sum(omqbar);
+  lm = warp_sum(lm);
+  const size_t k = (size_t)w * L.Nx + x, wn = 2 * (size_t)L.Nx;
+  const double omq = c.omq[k];
+  const double taub = -omqbar * omq * omq;  // omq = 1/tau_q
+  if (lane < 18) {
+    const int sp = lane >= 9 ? 1 : 0;
     const int jw = w == 0 ? 0 : L.N - 1;
-    double g[2][9], gb[2][9] = {};
-    pull(L, fin, c.r, c.kappa, x, jw, g);
-    const double omq = c.omq[w * L.Nx + x];
-    const double taub = -omqbar * omq * omq;  // omq = 1/tau_q
-    double ab = 0, lmb = 0;
-    tau_q(L, g, alpha[w * L.Nx + x], taub, gb, &ab, &lmb);
-    #pragma unroll
-    for (int sp = 0; sp < 2; ++sp)
-      #pragma unroll
-      for (int i = 0; i < 9; ++i) gbar[fidx(L, sp, i, jw, x)] += gb[sp][i];
-    alphabar[w * L.Nx + x] += ab;
-    lnmu_col[w * L.Nx + x] += lmb;
+    gbar[fidx(L, sp, lane - 9 * sp, jw, x)] += taub * (c.dq[k] + c.dq[wn + k] * L.s[sp]);
+  }
+  if (lane == 0) {
+    alphabar[k] += taub * c.dq[2 * wn + k];
+    lnmu_col[k] += lm;
+    lnmu_col[k] += taub * c.dq[3 * wn + k];
   }
 }
 
 // Transpose of Pull: lam_prev(x, j) gathers the gbar of every node that
-// pulled population i of node (x, j) - plainly, through the DBB rule of its
-// own wall row, or through a ghost column - and the DBB rule's r adjoint is
-// carried into the wall node's densities and accommodation.  The kappa
-// terms are added by adj_rev_kappa_kernel.
-__global__ void adj_rev_pull_kernel(AL L, const double* __restrict__ fin,
-                                    const double* __restrict__ alpha, StepCols c,
-                                    const double* __restrict__ gbar, double* __restrict__ lamp,
-                                    double* __restrict__ alphabar) {
+// pulled population i of node (x, j) plainly or through the DBB rule of its
+// own wall row, and the DBB rule's r adjoint is carried into the wall node's
+// densities and accommodation.  The ghost-column and kappa terms of the
+// ends are added by adj_rev_kappa_kernel.  Every gather loads from an
+// address inside the array whether or not its source exists (the value is
+// then dropped), so the 18 loads are independent of one another.
+__global__ void __launch_bounds__(128) adj_rev_pull_kernel(
+    AL L, const double* __restrict__ fin, const double* __restrict__ alpha, StepCols c,
+    const double* __restrict__ gbar, double* __restrict__ lamp, double* __restrict__ alphabar) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (x >= L.Nx) return;
@@ -924,21 +970,10 @@ __global__ void adj_rev_pull_kernel(AL L, const double* __restrict__ fin,
   for (int sp = 0; sp < 2; ++sp)
     #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      double v = 0.0;
-      const int xd = wrapx(L, x + CXd[i]), jd = j + CYd[i];
-      if (jd >= 0 && jd < L.N && interior(L, xd)) v += gbar[fidx(L, sp, i, jd, xd)];
-      if (!L.x_periodic) {
-        const bool in_c = (CXd[i] == 1), out_c = (CXd[i] == -1);
-        if (in_c && jd >= 0 && jd < L.N) {
-          if (x == 1) v += 2.0 * c.kappa[sp] * gbar[fidx(L, sp, i, jd, 1)];
-          if (x == 2) v -= c.kappa[sp] * gbar[fidx(L, sp, i, jd, 1)];
-        }
-        if (out_c && jd >= 0 && jd < L.N) {
-          if (x == L.Nx - 2) v += 2.0 * c.kappa[2 + sp] * gbar[fidx(L, sp, i, jd, L.Nx - 2)];
-          if (x == L.Nx - 3) v -= c.kappa[2 + sp] * gbar[fidx(L, sp, i, jd, L.Nx - 2)];
-        }
-      }
-      lp[sp][i] = v;
+      const int xd = wrapx(L, x + cxd(i)), jd = j + cyd(i);
+      const bool ok = jd >= 0 && jd < L.N && interior(L, xd);
+      const double v = gbar[fidx(L, sp, i, ok ? jd : j, ok ? xd : x)];
+      lp[sp][i] = ok ? v : 0.0;
     }
   // diffuse bounce-back: the unknowns (2, 5, 6) at row 0 and (4, 7, 8) at
   // row N-1 are pulled from this node's own outgoing populations
@@ -976,11 +1011,12 @@ __global__ void adj_rev_pull_kernel(AL L, const double* __restrict__ fin,
     for (int i = 0; i < 9; ++i) lamp[fidx(L, sp, i, j, x)] = lp[sp][i];
 }
 
-// kappa adjoints (reduced over the end columns' rows), their terms in
-// lam_prev at columns 1, 2 and N_x - 2, N_x - 3, and the theta adjoint of
-// rho_in, fixed order.  Block e of a 4-block launch handles one (end,
-// species) pair e = 2 end + species; a 1-block launch handles all four in
-// turn (needed when N_x < 6, where the columns of the two ends overlap).
+// The ends in reverse: kappa adjoints (reduced over the end columns' rows),
+// the ghost-column terms and kappa terms of lam_prev at columns 1, 2 and
+// N_x - 2, N_x - 3, and the theta adjoint of rho_in, fixed order.  Block e
+// of a 4-block launch handles one (end, species) pair e = 2 end + species; a
+// 1-block launch handles all four in turn (needed when N_x < 6, where the
+// columns of the two ends overlap).  Threads take (row, population) items;
 // theta_acc[species] collects the inlet's theta adjoint.
 __global__ void __launch_bounds__(256) adj_rev_kappa_kernel(
     AL L, const double* __restrict__ fin, StepCols c, const double* __restrict__ gbar,
@@ -989,33 +1025,39 @@ __global__ void __launch_bounds__(256) adj_rev_kappa_kernel(
   const int t = threadIdx.x;
   if (L.x_periodic) return;
   const int e0 = gridDim.x == 4 ? blockIdx.x : 0, e1 = gridDim.x == 4 ? blockIdx.x + 1 : 4;
+  const int items = 9 * L.N;
   for (int e = e0; e < e1; ++e) {
     const int sp = e & 1, inlet = e < 2;
     const int x1 = inlet ? 1 : L.Nx - 2, x2 = inlet ? 2 : L.Nx - 3, dir = inlet ? 1 : -1;
+    const double kap = c.kappa[e];
+    // node (x1, jd) pulled population i (c_ix = dir) from the ghost column:
+    // kappa (2 f(x1, js) - f(x2, js)), js = jd - c_iy
     double acc = 0.0, cs1 = 0.0, cs2 = 0.0;
-    for (int jd = t; jd < L.N; jd += blockDim.x) {
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const int js = jd - CYd[i];
-        if (CXd[i] == dir && js >= 0 && js < L.N)
-          acc += gbar[fidx(L, sp, i, jd, x1)] *
-                 (2.0 * fin[fidx(L, sp, i, js, x1)] - fin[fidx(L, sp, i, js, x2)]);
-        cs1 += fin[fidx(L, sp, i, jd, x1)];
-        cs2 += fin[fidx(L, sp, i, jd, x2)];
-      }
+    for (int k = t; k < items; k += blockDim.x) {
+      const int jd = k / 9, i = k - 9 * jd;
+      const int js = jd - cyd(i);
+      const bool ok = cxd(i) == dir && js >= 0 && js < L.N;
+      const int jsc = ok ? js : jd;
+      const double gb = gbar[fidx(L, sp, i, jd, x1)];
+      const double a1 = fin[fidx(L, sp, i, jsc, x1)], a2 = fin[fidx(L, sp, i, jsc, x2)];
+      acc += ok ? gb * (2.0 * a1 - a2) : 0.0;
+      cs1 += fin[fidx(L, sp, i, jd, x1)];
+      cs2 += fin[fidx(L, sp, i, jd, x2)];
     }
     const double kb = block_sum256(acc, sm);
     const double D = block_sum256(2.0 * cs1 - cs2, sm);
     // kappa_in = N rho_in / D, rho_in,s = theta C_s m_s
-    if (inlet && t == 0) theta_acc[sp] += kb * c.kappa[e] / L.theta;
+    if (inlet && t == 0) theta_acc[sp] += kb * kap / L.theta;
     // d kappa / d f(x, j) = -kappa / D * (2 at column 1 (N_x-2), -1 at column 2 (N_x-3))
-    const double gk = -kb * c.kappa[e] / D;
-    for (int jd = t; jd < L.N; jd += blockDim.x) {
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        lamp[fidx(L, sp, i, jd, x1)] += 2.0 * gk;
-        lamp[fidx(L, sp, i, jd, x2)] -= gk;
-      }
+    const double gk = -kb * kap / D;
+    for (int k = t; k < items; k += blockDim.x) {
+      const int j = k / 9, i = k - 9 * j;
+      const int jd = j + cyd(i);
+      const bool ok = cxd(i) == dir && jd >= 0 && jd < L.N;
+      const double gv = gbar[fidx(L, sp, i, ok ? jd : j, x1)];
+      const double gh = (ok ? kap * gv : 0.0) + gk;
+      lamp[fidx(L, sp, i, j, x1)] += 2.0 * gh;
+      lamp[fidx(L, sp, i, j, x2)] -= gh;
     }
     __syncthreads();  // the next pair's columns may be this pair's (N_x < 6)
   }
@@ -1094,7 +1136,11 @@ struct lbm_adj {
   bool own_stream = false;
   size_t S = 0;      // doubles per state
   double* ckpt = nullptr;   // [ceil(T/K)+1][S] states at steps 0, K, 2K, ...
-  double* seg[2] = {nullptr, nullptr};      // [K][S] replayed inputs of one segment's steps
+  int nseg = 0;      // checkpoint intervals, ceil(T/K)
+  // Buffer set b (two sets, one when nseg == 1) holds one interval's step
+  // inputs, column data and Psi values: the backward sweep replays into
+  // them; the forward run fills set (nseg - 1) & 1 with the last interval.
+  double* seg[2] = {nullptr, nullptr};      // [K][S] inputs of one segment's steps
   double* segcols[2] = {nullptr, nullptr};  // [K][4 Nx + 4] column data of those steps
   double* segpsi[2] = {nullptr, nullptr};   // [K][6][N][Nx] Psi values of those steps
   cudaStream_t rstream = nullptr;   // the replays of the backward sweep
@@ -1105,13 +1151,15 @@ struct lbm_adj {
   double* dtheta0 = nullptr;  // d f^0 / d theta
   double* alpha = nullptr;    // [2][Nx]
   double* alphabar = nullptr;
-  double* part_rev = nullptr;  // [ceil(N/REV_ROWS)][3][Nx] row-block partials
+  double* part_rev = nullptr;  // [N][2][Nx] per-row partials of adj_rev_node_kernel
+  int rows_step = 1, rows_rev = 1;  // rows per block of the two node kernels (node_rows)
   double* lnmu_col = nullptr; // [2][Nx] (per wall)
   double* theta_acc = nullptr;  // [2] (per species)
   double* colsum = nullptr;   // [3][Nx]
   double* part = nullptr;     // [256]
   double* h_col = nullptr;    // host copy of colsum
   bool have_forward = false;
+  bool kept = false;  // set (nseg - 1) & 1 holds the last interval of the forward run
   double CL = 0, flux = 0, Sl = 0, Sh = 0;
   int xstar = -1;
 };
@@ -1123,7 +1171,25 @@ StepCols cols_of(lbm_adj* a, double* base) {
   c.r = base;
   c.omq = base + 2 * a->L.Nx;
   c.kappa = base + 4 * a->L.Nx;
+  c.dq = base + 4 * a->L.Nx + 4;
   return c;
+}
+
+// Rows per block of a node kernel launched with one-warp blocks of 32
+// columns: the fewest rows for which every block is resident at once (the
+// occupancy calculator's blocks per SM times the SMs), so that the FP64
+// work is spread evenly, with no partial second wave.
+cudaError_t node_rows(const void* kernel, int Nx, int N, int* rows) {
+  int dev = 0, nsm = 0, occ = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 32, 0);
+  if (e != cudaSuccess) return e;
+  const long slots = (long)nsm * (occ > 0 ? occ : 1), ncb = (Nx + 31) / 32;
+  int r = 1;
+  while (r < N && ncb * ((N + r - 1) / r) > slots) ++r;
+  *rows = r;
+  return cudaSuccess;
 }
 
 // Forward step from f (input) into fo, column data into cols, on stream st.
@@ -1131,14 +1197,13 @@ int fwd_step(lbm_adj* a, const double* f, double* fo, StepCols c, cudaStream_t s
              double* psi_out = nullptr) {
   const AL& L = a->L;
   adj_kappa_kernel<<<4, 256, 0, st>>>(L, f, c.kappa);
-  const int cb = (L.Nx + 127) / 128;
   // one thread per (column, wall): small blocks spread the FP64 work of
   // the wall columns over many SMs
   const dim3 wg((L.Nx + 31) / 32, 2);
   adj_cols_kernel<<<wg, 32, 0, st>>>(L, f, a->alpha, c);
   adj_tauq_kernel<<<wg, 32, 0, st>>>(L, f, a->alpha, c);
-  dim3 grd(cb, L.N);
-  adj_step_kernel<<<grd, 128, 0, st>>>(L, f, fo, c, psi_out);
+  adj_step_kernel<<<dim3((L.Nx + 31) / 32, (L.N + a->rows_step - 1) / a->rows_step), 32, 0, st>>>(
+      L, f, fo, c, psi_out, a->rows_step);
   CKA(cudaGetLastError());
   return LBM_OK;
 }
@@ -1205,13 +1270,14 @@ int lbm_adj_create(const lbm_mix_params* p, long nsteps, int checkpoint_every, v
     }
     a->own_stream = true;
   }
-  const long nck = (nsteps + a->K - 1) / a->K + 1;
-  const size_t cw = 4 * (size_t)Nx + 4;
+  a->nseg = (int)((nsteps + a->K - 1) / a->K);
+  const long nck = a->nseg + 1;
+  const size_t cw = cols_width(Nx);
   cudaError_t e = cudaSuccess;
 #define ALLOCA(ptr, bytes) \
   if (e == cudaSuccess) e = cudaMalloc((void**)&(ptr), (bytes))
   ALLOCA(a->ckpt, sizeof(double) * a->S * nck);
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < (a->nseg > 1 ? 2 : 1); ++b) {
     ALLOCA(a->seg[b], sizeof(double) * a->S * a->K);
     ALLOCA(a->segcols[b], sizeof(double) * cw * a->K);
     ALLOCA(a->segpsi[b], sizeof(double) * 6 * (size_t)p->N * Nx * a->K);
@@ -1230,7 +1296,7 @@ int lbm_adj_create(const lbm_mix_params* p, long nsteps, int checkpoint_every, v
   ALLOCA(a->dtheta0, sizeof(double) * a->S);
   ALLOCA(a->alpha, sizeof(double) * 2 * Nx);
   ALLOCA(a->alphabar, sizeof(double) * 2 * Nx);
-  ALLOCA(a->part_rev, sizeof(double) * 3 * Nx * (size_t)((p->N + REV_ROWS - 1) / REV_ROWS));
+  ALLOCA(a->part_rev, sizeof(double) * 2 * Nx * (size_t)p->N);
   ALLOCA(a->lnmu_col, sizeof(double) * 2 * Nx);
   ALLOCA(a->theta_acc, sizeof(double) * 2);
   ALLOCA(a->colsum, sizeof(double) * 3 * Nx);
@@ -1248,6 +1314,8 @@ int lbm_adj_create(const lbm_mix_params* p, long nsteps, int checkpoint_every, v
       free(al);
     }
   }
+  if (e == cudaSuccess) e = node_rows((const void*)adj_step_kernel, Nx, p->N, &a->rows_step);
+  if (e == cudaSuccess) e = node_rows((const void*)adj_rev_node_kernel, Nx, p->N, &a->rows_rev);
   if (e != cudaSuccess) {
     const int code = e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
     lbm_internal_error(code, "adjoint allocation failed: %s", cudaGetErrorString(e));
@@ -1309,10 +1377,29 @@ int lbm_adj_forward(lbm_adj* a, double* CL, double* flux) {
   const dim3 grd((L.Nx + 127) / 128, L.N);
   adj_init_kernel<<<grd, 128, 0, a->stream>>>(L, a->ckpt, a->dtheta0);
   CKA(cudaGetLastError());
+  a->have_forward = false;
+  a->kept = false;
+  // The last interval's steps keep their inputs, column data and Psi values
+  // in buffer set bl, so that the backward sweep need not replay it (with
+  // one interval, checkpoint_every >= nsteps, it replays nothing).
+  const long tl0 = (long)(a->nseg - 1) * a->K;
+  const int bl = (a->nseg - 1) & 1;
+  const size_t cw = cols_width(L.Nx), psi_step = 6 * (size_t)L.N * L.Nx;
   const double* f = a->ckpt;
   for (long t = 1; t <= a->T; ++t) {
     double* fo = (t % a->K == 0) ? a->ckpt + a->S * (size_t)(t / a->K) : a->work[t & 1];
-    int st = fwd_step(a, f, fo, cols_of(a, a->segcols[0]), a->stream);
+    int st;
+    if (t > tl0) {
+      const long k = t - tl0 - 1;
+      if (k == 0)  // f^{tl0} is a checkpoint; the interval's first input
+        CKA(cudaMemcpyAsync(a->seg[bl], f, sizeof(double) * a->S, cudaMemcpyDeviceToDevice,
+                            a->stream));
+      if (t < a->T) fo = a->seg[bl] + a->S * (size_t)(k + 1);
+      st = fwd_step(a, a->seg[bl] + a->S * (size_t)k, fo, cols_of(a, a->segcols[bl] + cw * k),
+                    a->stream, a->segpsi[bl] + psi_step * (size_t)k);
+    } else {
+      st = fwd_step(a, f, fo, cols_of(a, a->segcols[0]), a->stream);
+    }
     if (st) return st;
     f = fo;
   }
@@ -1320,6 +1407,7 @@ int lbm_adj_forward(lbm_adj* a, double* CL, double* flux) {
   if (st) return st;
   if (!isfinite(a->CL)) return lbm_internal_error(LBM_ENONFINITE, "non-finite forward state");
   a->have_forward = true;
+  a->kept = true;
   if (CL) *CL = a->CL;
   if (flux) *flux = a->flux;
   return LBM_OK;
@@ -1346,14 +1434,14 @@ int lbm_adj_gradient(lbm_adj* a, int objective, double* dtheta, double* dkn, dou
   if (dalpha && n_alpha != 2L * L.Nx)
     return lbm_internal_error(LBM_EINVAL, "dalpha needs 2 N_x = %d values", 2 * L.Nx);
   const dim3 grd((L.Nx + 127) / 128, L.N);
-  const size_t cw = 4 * (size_t)L.Nx + 4;
+  const size_t cw = cols_width(L.Nx);
   CKA(cudaMemsetAsync(a->alphabar, 0, sizeof(double) * 2 * L.Nx, a->stream));
   CKA(cudaMemsetAsync(a->lnmu_col, 0, sizeof(double) * 2 * L.Nx, a->stream));
   CKA(cudaMemsetAsync(a->theta_acc, 0, sizeof(double) * 2, a->stream));
   adj_seed_kernel<<<grd, 128, 0, a->stream>>>(L, objective, a->xstar, a->Sl, a->Sh, a->lam[0]);
   CKA(cudaGetLastError());
   int cur = 0;  // lam[cur] is the adjoint of the state after the step being reversed
-  const long nseg = (a->T + a->K - 1) / a->K;
+  const long nseg = a->nseg;
   // the replay's last output of a segment is not needed (only its column
   // data are); it goes to the work buffer that does not hold f^T, so that
   // lbm_adj_state still returns the forward run's final state afterwards
@@ -1384,26 +1472,32 @@ int lbm_adj_gradient(lbm_adj* a, int objective, double* dtheta, double* dkn, dou
   // is the same bit for bit.
   CKA(cudaEventRecord(a->ev_start, a->stream));
   CKA(cudaStreamWaitEvent(a->rstream, a->ev_start, 0));
-  int st0 = replay(nseg - 1);
+  // the forward run left the last interval in its buffer set
+  const bool last_kept = a->kept;
+  int st0 = last_kept ? LBM_OK : replay(nseg - 1);
   if (st0) return st0;
+  // a replay into the last interval's set (segment nseg - 3, ...) ends it
+  if (nseg >= 3) a->kept = false;
   for (long sg = nseg - 1; sg >= 0; --sg) {
     const int b = (int)(sg & 1);
     if (sg >= 1) {
       if (sg + 1 <= nseg - 1) CKA(cudaStreamWaitEvent(a->rstream, a->ev_rev[(sg + 1) & 1], 0));
       if ((st0 = replay(sg - 1))) return st0;
     }
-    CKA(cudaStreamWaitEvent(a->stream, a->ev_rep[b], 0));
+    if (!(last_kept && sg == nseg - 1)) CKA(cudaStreamWaitEvent(a->stream, a->ev_rep[b], 0));
     const long t0 = sg * a->K;
     const long t1 = (t0 + a->K < a->T) ? t0 + a->K : a->T;
     for (long t = t1; t > t0; --t) {
       const long k = t - t0 - 1;
       const double* fin = a->seg[b] + a->S * (size_t)k;
       StepCols c = cols_of(a, a->segcols[b] + cw * k);
-      const int nparts = (L.N + REV_ROWS - 1) / REV_ROWS;
-      adj_rev_node_kernel<<<dim3((L.Nx + 31) / 32, nparts), dim3(32, 4), 0, a->stream>>>(
-          L, fin, a->lam[cur], c, a->segpsi[b] + psi_step * (size_t)k, a->gbar, a->part_rev);
-      adj_rev_tauq_kernel<<<dim3((L.Nx + 31) / 32, 2), 32, 0, a->stream>>>(
-          L, fin, a->alpha, c, a->part_rev, nparts, a->gbar, a->alphabar, a->lnmu_col);
+      adj_rev_node_kernel<<<dim3((L.Nx + 31) / 32, (L.N + a->rows_rev - 1) / a->rows_rev), 32, 0,
+                            a->stream>>>(L, fin, a->lam[cur], c,
+                                         a->segpsi[b] + psi_step * (size_t)k, a->rows_rev,
+                                         a->gbar, a->part_rev);
+      adj_rev_tauq_kernel<<<(2 * L.Nx + kRevTauqWarps - 1) / kRevTauqWarps, 32 * kRevTauqWarps,
+                            0, a->stream>>>(
+          L, c, a->part_rev, a->gbar, a->alphabar, a->lnmu_col);
       adj_rev_pull_kernel<<<grd, 128, 0, a->stream>>>(L, fin, a->alpha, c, a->gbar,
                                                       a->lam[1 - cur], a->alphabar);
       // one block per (end, species) unless the end columns overlap

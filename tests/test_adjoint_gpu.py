@@ -145,9 +145,12 @@ def test_gradient_against_fd_of_the_oracle(obj):
 
 
 def test_checkpoint_interval_does_not_change_the_gradient():
+    """One interval (the forward run keeps every step: nothing is replayed),
+    two (the last is kept, the first replayed) or many: the same gradient,
+    bit for bit."""
     al = _alpha(SMALL["N_x"])
     out = []
-    for ck in (1, 7, 300):
+    for ck in (1, 7, 150, 300, 1000):
         a = binding.LbmAdjoint(SMALL, STEPS, ck, al)
         a.forward()
         out.append(a.gradient(binding.LBM_ADJ_CL))
@@ -156,7 +159,27 @@ def test_checkpoint_interval_does_not_change_the_gradient():
         assert np.array_equal(g["alpha"], out[0]["alpha"])
 
 
-@pytest.mark.parametrize("steps,ckpt", [(300, 7), (301, 7), (300, 30), (10, 4)])
+@pytest.mark.parametrize("ckpt", [7, 150, 300])
+def test_repeated_gradients(ckpt):
+    """Gradients of both objectives after one forward run, in turn and again:
+    each equals the one of a fresh handle (the interval the forward run kept
+    is replayed again once a backward sweep has reused its buffers)."""
+    al = _alpha(SMALL["N_x"])
+    fresh = {}
+    for obj in (binding.LBM_ADJ_CL, binding.LBM_ADJ_FLUX):
+        a = binding.LbmAdjoint(SMALL, STEPS, ckpt, al)
+        a.forward()
+        fresh[obj] = a.gradient(obj)
+    a = binding.LbmAdjoint(SMALL, STEPS, ckpt, al)
+    a.forward()
+    for obj in (binding.LBM_ADJ_CL, binding.LBM_ADJ_FLUX, binding.LBM_ADJ_CL):
+        g = a.gradient(obj)
+        assert g["theta"] == fresh[obj]["theta"] and g["Kn_out"] == fresh[obj]["Kn_out"]
+        assert np.array_equal(g["alpha"], fresh[obj]["alpha"])
+
+
+@pytest.mark.parametrize("steps,ckpt", [(300, 7), (301, 7), (300, 30), (10, 4), (300, 300),
+                                        (301, 1000), (301, 151)])
 def test_state_is_kept_through_the_gradient(steps, ckpt):
     """The backward sweep replays every checkpoint interval; the final state
     of the forward run must survive it, whatever the parity of the step count
