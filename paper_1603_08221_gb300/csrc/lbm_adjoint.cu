@@ -385,28 +385,52 @@ struct NodeFwd {
   double m[2][9], meq[2][9];
 };
 
-// Rows of M in the order rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy
-// (Eq. m) and the diagonal of M M^T.
-__device__ __forceinline__ double Mki(int k, int i) {
-  const int cx = cxd(i), cy = cyd(i);
-  const int c2 = cx * cx + cy * cy;
-  switch (k) {
-    case 0: return 1.0;
-    case 1: return -4.0 + 3.0 * c2;
-    case 2: return 4.0 - 10.5 * c2 + 4.5 * c2 * c2;
-    case 3: return cx;
-    case 4: return (3.0 * c2 - 5.0) * cx;
-    case 5: return cy;
-    case 6: return (3.0 * c2 - 5.0) * cy;
-    case 7: return cx * cx - cy * cy;
-    default: return cx * cy;
-  }
-}
 // 1 / |M_k|^2, the diagonal of (M M^T)^-1.
 __device__ __forceinline__ double inv_Mnorm(int k) {
   const double w[9] = {1.0 / 9.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 6.0, 1.0 / 12.0,
                        1.0 / 6.0, 1.0 / 12.0, 1.0 / 4.0, 1.0 / 4.0};
   return w[k];
+}
+
+// m = M v, M the matrix of Eq. m with rows rho, e, eps, j_x, q_x, j_y, q_y,
+// p_xx, p_xy, factored over the rest, axis and diagonal classes and their
+// sums and differences: 33 FP64 operations instead of one per nonzero entry
+// of M (tests/test_adjoint_mrt.py evaluates this code against M).
+__device__ __forceinline__ void mrt_fwd(const double v[9], double m[9]) {
+  const double a14 = (v[1] + v[2]) + (v[3] + v[4]);
+  const double a58 = (v[5] + v[6]) + (v[7] + v[8]);
+  m[0] = v[0] + a14 + a58;
+  m[1] = fma(-4.0, v[0], fma(2.0, a58, -a14));  // -4 v0 - a14 + 2 a58
+  m[2] = fma(4.0, v[0], fma(-2.0, a14, a58));   // 4 v0 - 2 a14 + a58
+  const double d13 = v[1] - v[3], d24 = v[2] - v[4];
+  const double dx = (v[5] - v[6]) + (v[8] - v[7]);  // diagonal c_x
+  const double dy = (v[5] - v[7]) + (v[6] - v[8]);  // diagonal c_y
+  m[3] = d13 + dx;
+  m[4] = fma(-2.0, d13, dx);
+  m[5] = d24 + dy;
+  m[6] = fma(-2.0, d24, dy);
+  m[7] = (v[1] + v[3]) - (v[2] + v[4]);
+  m[8] = (v[5] + v[7]) - (v[6] + v[8]);
+}
+
+// o = M^T d, factored the same way (24 FP64 operations).
+__device__ __forceinline__ void mrt_tr(const double d[9], double o[9]) {
+  o[0] = fma(4.0, d[2] - d[1], d[0]);            // d0 - 4 d1 + 4 d2
+  const double B = fma(-2.0, d[2], d[0] - d[1]);  // axis: d0 - d1 - 2 d2
+  const double xa = fma(-2.0, d[4], d[3]), ya = fma(-2.0, d[6], d[5]);
+  const double Bp = B + d[7], Bm = B - d[7];
+  o[1] = Bp + xa;
+  o[3] = Bp - xa;
+  o[2] = Bm + ya;
+  o[4] = Bm - ya;
+  const double A = fma(2.0, d[1], d[0] + d[2]);   // diagonal: d0 + 2 d1 + d2
+  const double X = d[3] + d[4], Y = d[5] + d[6];
+  const double P = A + d[8], Q = A - d[8];
+  const double sp = X + Y, sm = X - Y;
+  o[5] = P + sp;
+  o[7] = P - sp;
+  o[6] = Q - sm;
+  o[8] = Q + sm;
 }
 
 // Psi(y) = (psi(y/lambda) + psi((H-y)/lambda)) / 2 and dPsi/dlambda, from
@@ -428,16 +452,10 @@ __device__ void node_forward(const AL& L, const double g[2][9], double y, double
                              double* psi_out = nullptr, size_t plane = 0) {
   #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
-    double r = 0, jx = 0, jy = 0;
-    #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      r += g[sp][i];
-      jx = macc(jx, cxd(i), g[sp][i]);
-      jy = macc(jy, cyd(i), g[sp][i]);
-    }
-    F.rho[sp] = r;
-    F.jx[sp] = jx;
-    F.jy[sp] = jy;
+    mrt_fwd(g[sp], F.m[sp]);  // rho_s, j_x, j_y are rows 0, 3, 5
+    F.rho[sp] = F.m[sp][0];
+    F.jx[sp] = F.m[sp][3];
+    F.jy[sp] = F.m[sp][5];
   }
   F.rho_t = F.rho[0] + F.rho[1];
   F.inv_rt = 1.0 / F.rho_t;
@@ -489,23 +507,15 @@ __device__ void node_forward(const AL& L, const double g[2][9], double y, double
     const double r = F.rho[sp], s = L.s[sp];
     const double br[9] = {1.0, -4.0 + 2.0 * s + 3.0 * u2, 4.0 - 3.0 * s - 3.0 * u2, F.ux,
                           -F.ux, F.uy, -F.uy, F.ux * F.ux - F.uy * F.uy, F.ux * F.uy};
-    double dl[9];
+    double dl[9], c[9];
     #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      double mk = 0;
-      #pragma unroll
-      for (int i = 0; i < 9; ++i) mk = macc(mk, Mki(k, i), g[sp][i]);
-      F.m[sp][k] = mk;
       F.meq[sp][k] = r * br[k];
-      dl[k] = S[k] * (mk - F.meq[sp][k]) * inv_Mnorm(k);
+      dl[k] = S[k] * (F.m[sp][k] - F.meq[sp][k]) * inv_Mnorm(k);
     }
+    mrt_tr(dl, c);
     #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      double c = 0;
-      #pragma unroll
-      for (int k = 0; k < 9; ++k) c = macc(c, Mki(k, i), dl[k]);
-      fo[sp][i] = g[sp][i] - c;
-    }
+    for (int i = 0; i < 9; ++i) fo[sp][i] = g[sp][i] - c[i];
   }
 }
 
@@ -520,32 +530,24 @@ __device__ void node_reverse(const AL& L, const double g[2][9], double y, double
   node_forward(L, g, y, omq, F, fo, psi_in, nullptr, plane);
   const double S[9] = {0.0, L.om_e, L.om_eps, F.om_d, omq, F.om_d, omq, F.om_s, F.om_s};
   double Sbar[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  double rhob[2] = {0, 0}, jxb[2] = {0, 0}, jyb[2] = {0, 0};
+  double rhob[2] = {0, 0};
   double uxb = 0, uyb = 0;
   const double u2 = F.ux * F.ux + F.uy * F.uy;
+  // adjoint of the moments m = M g; its rows 0, 3, 5 (rho_s, j_x, j_y) also
+  // collect the mixture terms below, and gbar = fbar + M^T mbar at the end
+  double mbar[2][9];
   #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     const double r = F.rho[sp], s = L.s[sp];
-    #pragma unroll
-    for (int i = 0; i < 9; ++i) gbar[sp][i] = fbar[sp][i];
     // f_i = g_i - sum_k M_ki dl_k, dl_k = S_k (m_k - meq_k) / |M_k|^2
-    double mbar[9], meqbar[9];
+    double Mf[9], meqbar[9];
+    mrt_fwd(fbar[sp], Mf);
     #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      double dlb = 0;
-      #pragma unroll
-      for (int i = 0; i < 9; ++i) dlb = macc(dlb, -Mki(k, i), fbar[sp][i]);
-      dlb *= inv_Mnorm(k);
-      mbar[k] = S[k] * dlb;
+      const double dlb = -Mf[k] * inv_Mnorm(k);
+      mbar[sp][k] = S[k] * dlb;
       meqbar[k] = -S[k] * dlb;
       Sbar[k] += (F.m[sp][k] - F.meq[sp][k]) * dlb;
-    }
-    #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      double c = 0;
-      #pragma unroll
-      for (int k = 0; k < 9; ++k) c = macc(c, Mki(k, i), mbar[k]);
-      gbar[sp][i] += c;
     }
     // meq = rho_s (1, -4 + 2s + 3u^2, 4 - 3s - 3u^2, ux, -ux, uy, -uy, ux^2 - uy^2, ux uy)
     const double br[9] = {1.0, -4.0 + 2.0 * s + 3.0 * u2, 4.0 - 3.0 * s - 3.0 * u2, F.ux,
@@ -598,11 +600,13 @@ __device__ void node_reverse(const AL& L, const double g[2][9], double y, double
   #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     rhob[sp] += rhotb + nb * L.s[sp];
-    jxb[sp] += Jxb;
-    jyb[sp] += Jyb;
+    mbar[sp][0] += rhob[sp];
+    mbar[sp][3] += Jxb;
+    mbar[sp][5] += Jyb;
+    double c[9];
+    mrt_tr(mbar[sp], c);
     #pragma unroll
-    for (int i = 0; i < 9; ++i)
-      gbar[sp][i] += macc(macc(rhob[sp], cxd(i), jxb[sp]), cyd(i), jyb[sp]);
+    for (int i = 0; i < 9; ++i) gbar[sp][i] = fbar[sp][i] + c[i];
   }
   *lnmu_bar = lnmub;
 }
