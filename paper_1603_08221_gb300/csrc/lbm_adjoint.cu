@@ -774,9 +774,10 @@ __global__ void adj_tauq_kernel(AL L, const double* __restrict__ f, const double
 // One FP64 step over all nodes: f_out = Collide(Pull(f_in)).  One warp per
 // block, block (bx, by) covers 32 columns x `rows` rows (see node_rows).
 // psi_out (nullable): [6][N][Nx] Psi values of this step for the reverse
-// sweep (see node_forward).  At least 19 resident blocks per SM (ptxas then
-// keeps 96 registers and spills a few values to L1): 2888 blocks fit on 152
-// SMs, one row per block for the 2560 warps of a 1280 x 64 channel.
+// sweep (see node_forward).  Registers are allocated per SM sub-partition
+// (four of 16384): at the 96 this bound leaves (a few values spill to L1)
+// each holds five warps, 20 per SM, so one row per block fits the 2560
+// warps of a 1280 x 64 channel in one wave on 152 SMs.
 __global__ void __launch_bounds__(32, 19) adj_step_kernel(AL L, const double* __restrict__ fin,
                                                       double* __restrict__ fout, StepCols c,
                                                       double* __restrict__ psi_out, int rows) {
@@ -870,7 +871,10 @@ __global__ void adj_seed_kernel(AL L, int objective, int xs, double Sl, double S
 // 32 columns x `rows` rows (see node_rows: every block fits on the GPU at
 // once, so the SMs share the work to within one block).
 // psi: [6][N][Nx] Psi values the forward run or the replay of this step
-// stored.
+// stored.  At its 200 registers an SM sub-partition holds two warps, 8 per
+// SM, so node_rows gives the 1280 x 64 channel three rows per block (0.72
+// waves).  Capped at 168 registers (three warps per sub-partition, two rows
+// per block, 40 bytes spilled to L1) it ran 4 % slower.
 __global__ void __launch_bounds__(32) adj_rev_node_kernel(
     AL L, const double* __restrict__ fin, const double* __restrict__ lam, StepCols c,
     const double* __restrict__ psi, int rows, double* __restrict__ gbar,
