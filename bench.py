@@ -275,7 +275,7 @@ def run_adjoint(args, stream):
     alpha = workloads.random_accommodation(nx, 1).reshape(2, nx)
     steps = args.adjoint_steps
     # per kept step: the state (18 N N_x), Psi values (6 N N_x), column data
-    per_step = 8 * (24 * p["N"] * nx + 4 * nx + 4)
+    per_step = 8 * (24 * p["N"] * nx + 18 * nx + 4)
     free, _ = torch.cuda.mem_get_info()
     ck_lean = 70
     ck = steps if per_step * steps < 0.5 * free else ck_lean

@@ -401,13 +401,13 @@ typedef struct lbm_adj lbm_adj;
  * with the default readings) and allocates
  * the checkpoints (ceil(nsteps/checkpoint_every) + 1 states of 18 N N_x
  * doubles) and two intervals of step inputs, each step with 6 N N_x doubles
- * of wall-confinement factors and 4 N_x + 4 of column data (one interval
+ * of wall-confinement factors and 18 N_x + 4 of column data (one interval
  * when checkpoint_every >= nsteps).  The forward run keeps its last interval
  * there; the backward sweep replays each other interval on a second,
  * internal stream while it reverses the next, and the reverse reads the
  * factors the forward run or the replay evaluated.  With
  * checkpoint_every >= nsteps the forward run keeps every step (about
- * 8 (24 N N_x + 4 N_x) bytes per step) and nothing is replayed.
+ * 8 (24 N N_x + 18 N_x) bytes per step) and nothing is replayed.
  * stream: cudaStream_t or NULL for an own stream.  Errors: LBM_EINVAL,
  * LBM_ENOMEM, LBM_ECUDA. */
 int lbm_adj_create(const lbm_mix_params* p, long nsteps, int checkpoint_every, void* stream,

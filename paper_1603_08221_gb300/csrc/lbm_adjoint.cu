@@ -317,9 +317,10 @@ struct StepCols {
   double* omq;    // [2][Nx]
   double* kappa;  // [4]: in_a, in_b, out_a, out_b
   double* dq;     // [4][2][Nx]: d tau_q / d (rho_t, n, alpha, ln mu) per wall node
+  double* dr;     // [3][2][Nx]: d r / d (rho_a, rho_b, alpha) per wall node
 };
 // doubles of one step's column data
-__host__ __device__ inline size_t cols_width(int Nx) { return 12 * (size_t)Nx + 4; }
+__host__ __device__ inline size_t cols_width(int Nx) { return 18 * (size_t)Nx + 4; }
 
 // ----------------------------------------------------------------- pull
 // Source value of population i of species sp at (xs, js): the stored state,
@@ -732,18 +733,24 @@ __global__ void __launch_bounds__(256) adj_kappa_kernel(AL L, const double* __re
   }
 }
 
-// r of both walls and 1/tau_q of both halves per column.
-// r of wall w = blockIdx.y per column.
+// r of wall w = blockIdx.y per column, and its derivatives with respect to
+// the wall node's species densities and the accommodation coefficient
+// (c.dr, for the reverse of the DBB rule).
 __global__ void adj_cols_kernel(AL L, const double* __restrict__ f, const double* __restrict__ alpha,
                                 StepCols c) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, w = blockIdx.y;
   if (x >= L.Nx) return;
+  const size_t k = (size_t)w * L.Nx + x, wn = 2 * (size_t)L.Nx;
   if (!interior(L, x)) {
-    c.r[w * L.Nx + x] = 0.0;
-    c.omq[w * L.Nx + x] = 1.0;
+    c.r[k] = 0.0;
+    c.omq[k] = 1.0;
     return;
   }
-  c.r[w * L.Nx + x] = dbb_r(L, f, x, w == 0 ? 0 : L.N - 1, alpha[w * L.Nx + x], nullptr, nullptr);
+  double drr[2], dra;
+  c.r[k] = dbb_r(L, f, x, w == 0 ? 0 : L.N - 1, alpha[k], drr, &dra);
+  c.dr[k] = drr[0];
+  c.dr[wn + k] = drr[1];
+  c.dr[2 * wn + k] = dra;
 }
 // 1/tau_q of the half of wall w = blockIdx.y per column, and the
 // derivatives of tau_q the reverse sweep multiplies by the adjoint of tau_q
@@ -954,15 +961,17 @@ __global__ void __launch_bounds__(32 * kRevTauqWarps) adj_rev_tauq_kernel(
 }
 
 // Transpose of Pull: lam_prev(x, j) gathers the gbar of every node that
-// pulled population i of node (x, j) plainly or through the DBB rule of its
-// own wall row, and the DBB rule's r adjoint is carried into the wall node's
-// densities and accommodation.  The ghost-column and kappa terms of the
-// ends are added by adj_rev_kappa_kernel.  Every gather loads from an
+// pulled population i of node (x, j) plainly, through the DBB rule of its
+// own wall row or through a ghost column, and the DBB rule's r adjoint is
+// carried into the wall node's densities and accommodation (with the
+// derivatives of r the forward run stored).  Every gather loads from an
 // address inside the array whether or not its source exists (the value is
-// then dropped), so the 18 loads are independent of one another.
+// then dropped), so the loads are independent of one another; the FP64
+// work is a few multiply-adds per node, the FP64 pipe being narrow.
+// gk: [4] the kappa terms of adj_rev_kappa_kernel, per (end, species).
 __global__ void __launch_bounds__(128) adj_rev_pull_kernel(
-    AL L, const double* __restrict__ fin, const double* __restrict__ alpha, StepCols c,
-    const double* __restrict__ gbar, double* __restrict__ lamp, double* __restrict__ alphabar) {
+    AL L, const double* __restrict__ fin, StepCols c, const double* __restrict__ gbar,
+    const double* __restrict__ gk, double* __restrict__ lamp, double* __restrict__ alphabar) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (x >= L.Nx) return;
@@ -1005,13 +1014,39 @@ __global__ void __launch_bounds__(128) adj_rev_pull_kernel(
       lp[sp][out[2]] += (1.0 - r) * G2 + r * T;
       rbar += G0 * (-o0 + (2.0 / 3.0) * S) + G1 * (-o1 + S / 6.0) + G2 * (-o2 + S / 6.0);
     }
-    double drr[2], dra;
-    dbb_r(L, fin, x, j, alpha[w * L.Nx + x], drr, &dra);
+    const size_t k = (size_t)w * L.Nx + x, wn = 2 * (size_t)L.Nx;
     #pragma unroll
-    for (int sp = 0; sp < 2; ++sp)
+    for (int sp = 0; sp < 2; ++sp) {
+      const double v = rbar * c.dr[sp * wn + k];
       #pragma unroll
-      for (int i = 0; i < 9; ++i) lp[sp][i] += rbar * drr[sp];
-    alphabar[w * L.Nx + x] += rbar * dra;
+      for (int i = 0; i < 9; ++i) lp[sp][i] += v;
+    }
+    alphabar[k] += rbar * c.dr[2 * wn + k];
+  }
+  // the ends: node (x1, jd) pulled population i (c_ix pointing into the
+  // channel) from the ghost column kappa (2 f(x1) - f(x2)), and kappa itself
+  // depends on the columns x1 = 1, x2 = 2 (N_x - 2, N_x - 3) through gk
+  // (adj_rev_kappa_kernel): their transposes land in those columns
+  if (!L.x_periodic && (x <= 2 || x >= L.Nx - 3)) {
+    #pragma unroll
+    for (int end = 0; end < 2; ++end) {
+      const int x1 = end == 0 ? 1 : L.Nx - 2, x2 = end == 0 ? 2 : L.Nx - 3;
+      if (x != x1 && x != x2) continue;
+      const double wgt = x == x1 ? 2.0 : -1.0;
+      const int dir = end == 0 ? 1 : -1;
+      #pragma unroll
+      for (int sp = 0; sp < 2; ++sp) {
+        const int e = 2 * end + sp;
+        const double kap = c.kappa[e];
+        #pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          const int jd = j + cyd(i);
+          const bool ok = cxd(i) == dir && jd >= 0 && jd < L.N;
+          const double gv = gbar[fidx(L, sp, i, ok ? jd : j, x1)];
+          lp[sp][i] += wgt * ((ok ? kap * gv : 0.0) + gk[e]);
+        }
+      }
+    }
   }
   #pragma unroll
   for (int sp = 0; sp < 2; ++sp)
@@ -1019,55 +1054,42 @@ __global__ void __launch_bounds__(128) adj_rev_pull_kernel(
     for (int i = 0; i < 9; ++i) lamp[fidx(L, sp, i, j, x)] = lp[sp][i];
 }
 
-// The ends in reverse: kappa adjoints (reduced over the end columns' rows),
-// the ghost-column terms and kappa terms of lam_prev at columns 1, 2 and
-// N_x - 2, N_x - 3, and the theta adjoint of rho_in, fixed order.  Block e
-// of a 4-block launch handles one (end, species) pair e = 2 end + species; a
-// 1-block launch handles all four in turn (needed when N_x < 6, where the
-// columns of the two ends overlap).  Threads take (row, population) items;
-// theta_acc[species] collects the inlet's theta adjoint.
+// The ends in reverse: the adjoint of kappa_e for (end, species) e = blockIdx.x
+// = 2 end + species, reduced over the end columns' rows in a fixed order,
+// gives gk[e] = -kappa_bar kappa / D, the weight of d kappa / d f at columns
+// x1, x2 (times 2 and -1) that adj_rev_pull_kernel adds, and the inlet's
+// theta adjoint (theta_acc[species]).  Threads take (row, population)
+// items.
 __global__ void __launch_bounds__(256) adj_rev_kappa_kernel(
     AL L, const double* __restrict__ fin, StepCols c, const double* __restrict__ gbar,
-    double* __restrict__ lamp, double* __restrict__ theta_acc) {
+    double* __restrict__ gk, double* __restrict__ theta_acc) {
   __shared__ double sm[8];
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, e = blockIdx.x;
   if (L.x_periodic) return;
-  const int e0 = gridDim.x == 4 ? blockIdx.x : 0, e1 = gridDim.x == 4 ? blockIdx.x + 1 : 4;
-  const int items = 9 * L.N;
-  for (int e = e0; e < e1; ++e) {
-    const int sp = e & 1, inlet = e < 2;
-    const int x1 = inlet ? 1 : L.Nx - 2, x2 = inlet ? 2 : L.Nx - 3, dir = inlet ? 1 : -1;
-    const double kap = c.kappa[e];
-    // node (x1, jd) pulled population i (c_ix = dir) from the ghost column:
-    // kappa (2 f(x1, js) - f(x2, js)), js = jd - c_iy
-    double acc = 0.0, cs1 = 0.0, cs2 = 0.0;
-    for (int k = t; k < items; k += blockDim.x) {
-      const int jd = k / 9, i = k - 9 * jd;
-      const int js = jd - cyd(i);
-      const bool ok = cxd(i) == dir && js >= 0 && js < L.N;
-      const int jsc = ok ? js : jd;
-      const double gb = gbar[fidx(L, sp, i, jd, x1)];
-      const double a1 = fin[fidx(L, sp, i, jsc, x1)], a2 = fin[fidx(L, sp, i, jsc, x2)];
-      acc += ok ? gb * (2.0 * a1 - a2) : 0.0;
-      cs1 += fin[fidx(L, sp, i, jd, x1)];
-      cs2 += fin[fidx(L, sp, i, jd, x2)];
-    }
-    const double kb = block_sum256(acc, sm);
-    const double D = block_sum256(2.0 * cs1 - cs2, sm);
+  const int sp = e & 1, inlet = e < 2;
+  const int x1 = inlet ? 1 : L.Nx - 2, x2 = inlet ? 2 : L.Nx - 3, dir = inlet ? 1 : -1;
+  const double kap = c.kappa[e];
+  // node (x1, jd) pulled population i (c_ix = dir) from the ghost column:
+  // kappa (2 f(x1, js) - f(x2, js)), js = jd - c_iy
+  double acc = 0.0, cs1 = 0.0, cs2 = 0.0;
+  for (int k = t; k < 9 * L.N; k += blockDim.x) {
+    const int jd = k / 9, i = k - 9 * jd;
+    const int js = jd - cyd(i);
+    const bool ok = cxd(i) == dir && js >= 0 && js < L.N;
+    const int jsc = ok ? js : jd;
+    const double gb = gbar[fidx(L, sp, i, jd, x1)];
+    const double a1 = fin[fidx(L, sp, i, jsc, x1)], a2 = fin[fidx(L, sp, i, jsc, x2)];
+    acc += ok ? gb * (2.0 * a1 - a2) : 0.0;
+    cs1 += fin[fidx(L, sp, i, jd, x1)];
+    cs2 += fin[fidx(L, sp, i, jd, x2)];
+  }
+  const double kb = block_sum256(acc, sm);
+  const double D = block_sum256(2.0 * cs1 - cs2, sm);
+  if (t == 0) {
     // kappa_in = N rho_in / D, rho_in,s = theta C_s m_s
-    if (inlet && t == 0) theta_acc[sp] += kb * kap / L.theta;
-    // d kappa / d f(x, j) = -kappa / D * (2 at column 1 (N_x-2), -1 at column 2 (N_x-3))
-    const double gk = -kb * kap / D;
-    for (int k = t; k < items; k += blockDim.x) {
-      const int j = k / 9, i = k - 9 * j;
-      const int jd = j + cyd(i);
-      const bool ok = cxd(i) == dir && jd >= 0 && jd < L.N;
-      const double gv = gbar[fidx(L, sp, i, ok ? jd : j, x1)];
-      const double gh = (ok ? kap * gv : 0.0) + gk;
-      lamp[fidx(L, sp, i, j, x1)] += 2.0 * gh;
-      lamp[fidx(L, sp, i, j, x2)] -= gh;
-    }
-    __syncthreads();  // the next pair's columns may be this pair's (N_x < 6)
+    if (inlet) theta_acc[sp] += kb * kap / L.theta;
+    // d kappa / d f(x, j) = -kappa / D * (2 at column x1, -1 at column x2)
+    gk[e] = -kb * kap / D;
   }
 }
 
@@ -1163,6 +1185,7 @@ struct lbm_adj {
   int rows_step = 1, rows_rev = 1;  // rows per block of the two node kernels (node_rows)
   double* lnmu_col = nullptr; // [2][Nx] (per wall)
   double* theta_acc = nullptr;  // [2] (per species)
+  double* gk = nullptr;         // [4] kappa terms of the step being reversed
   double* colsum = nullptr;   // [3][Nx]
   double* part = nullptr;     // [256]
   double* h_col = nullptr;    // host copy of colsum
@@ -1180,6 +1203,7 @@ StepCols cols_of(lbm_adj* a, double* base) {
   c.omq = base + 2 * a->L.Nx;
   c.kappa = base + 4 * a->L.Nx;
   c.dq = base + 4 * a->L.Nx + 4;
+  c.dr = base + 12 * a->L.Nx + 4;
   return c;
 }
 
@@ -1307,6 +1331,7 @@ int lbm_adj_create(const lbm_mix_params* p, long nsteps, int checkpoint_every, v
   ALLOCA(a->part_rev, sizeof(double) * 2 * Nx * (size_t)p->N);
   ALLOCA(a->lnmu_col, sizeof(double) * 2 * Nx);
   ALLOCA(a->theta_acc, sizeof(double) * 2);
+  ALLOCA(a->gk, sizeof(double) * 4);
   ALLOCA(a->colsum, sizeof(double) * 3 * Nx);
   ALLOCA(a->part, sizeof(double) * 256);
 #undef ALLOCA
@@ -1360,6 +1385,7 @@ void lbm_adj_destroy(lbm_adj* a) {
   cudaFree(a->part_rev);
   cudaFree(a->lnmu_col);
   cudaFree(a->theta_acc);
+  cudaFree(a->gk);
   cudaFree(a->colsum);
   cudaFree(a->part);
   cudaFreeHost(a->h_col);
@@ -1506,11 +1532,10 @@ int lbm_adj_gradient(lbm_adj* a, int objective, double* dtheta, double* dkn, dou
       adj_rev_tauq_kernel<<<(2 * L.Nx + kRevTauqWarps - 1) / kRevTauqWarps, 32 * kRevTauqWarps,
                             0, a->stream>>>(
           L, c, a->part_rev, a->gbar, a->alphabar, a->lnmu_col);
-      adj_rev_pull_kernel<<<grd, 128, 0, a->stream>>>(L, fin, a->alpha, c, a->gbar,
-                                                      a->lam[1 - cur], a->alphabar);
-      // one block per (end, species) unless the end columns overlap
-      adj_rev_kappa_kernel<<<L.Nx >= 6 ? 4 : 1, 256, 0, a->stream>>>(
-          L, fin, c, a->gbar, a->lam[1 - cur], a->theta_acc);
+      // one block per (end, species); the pull adds its kappa terms
+      adj_rev_kappa_kernel<<<4, 256, 0, a->stream>>>(L, fin, c, a->gbar, a->gk, a->theta_acc);
+      adj_rev_pull_kernel<<<grd, 128, 0, a->stream>>>(L, fin, c, a->gbar, a->gk, a->lam[1 - cur],
+                                                      a->alphabar);
       CKA(cudaGetLastError());
       cur = 1 - cur;
     }
