@@ -42,7 +42,10 @@ RTOL_RHO = 1e-5
 RTOL_U = 1e-5
 ATOL_U = 3e-8
 K_MODEL = 3.0
-BF16_STEADY_CL = 0.10
+# the error model's bound on CL at steady state, relative to CL: the
+# emulated BF16 run of the 1024 x 16 fixture moves CL by 0.78 % (FP16: 0.49 %);
+# K_MODEL times that is 2.3 %
+BF16_STEADY_CL = 0.025
 FLOOR = dict(CL=1e-6, Cl_tilde=1e-6, Cl_profile=1e-6, mdot=1e-5, u=1e-5)
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
@@ -203,7 +206,7 @@ def test_sixteen_bit_against_oracle_one_eighth_copy(storage):
 def test_sixteen_bit_steady_state_against_oracle(storage):
     """The 1024 x 16 copy at steady state (206 000 steps): every recorded
     quantity within the error model, and CL within the stated bound of the
-    oracle's: 1 % for FP16, BF16_STEADY_CL for BF16."""
+    oracle's: 1 % for FP16, BF16_STEADY_CL (2.5 %) for BF16."""
     report, exact = _check_against_model("lowp_neon_argon_1024x16.txt", 16, (206000,), storage)
     err, _ = report[(206000, "CL")]
     cl = exact[(206000, "CL")][0]
