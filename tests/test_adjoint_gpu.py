@@ -124,6 +124,35 @@ def test_gradient_against_fd_of_the_fp64_map(obj):
         assert _rel(float(flat @ v), fd) < RTOL_GRAD
 
 
+@pytest.mark.parametrize("N,Nx", [(5, 5), (4, 6), (5, 7)])
+@pytest.mark.parametrize("obj", [binding.LBM_ADJ_CL, binding.LBM_ADJ_FLUX])
+def test_narrow_channels_against_fd_of_the_oracle(N, Nx, obj):
+    """Channels so short that the ends share columns (N_x = 5: column 2 is
+    the second column of both ends; N_x = 6: the ends touch) and odd row
+    counts: theta, Kn_out and every accommodation component against central
+    differences of the oracle."""
+    p = dict(m_a=workloads.HE, m_b=workloads.AR, C_l=0.5, theta=1.5, Kn_out=0.3, N=N, N_x=Nx)
+    steps = 60
+    al = _alpha(Nx, seed=2)
+    a = binding.LbmAdjoint(p, steps, 7, al)
+    a.forward()
+    g = a.gradient(obj)
+    J0 = _oracle_J(p, al, steps, obj)
+    for name in ("theta", "Kn_out"):
+        pp, pm = dict(p), dict(p)
+        pp[name] += H_FD
+        pm[name] -= H_FD
+        fd = (_oracle_J(pp, al, steps, obj) - _oracle_J(pm, al, steps, obj)) / (2 * H_FD)
+        assert _close(g[name], fd, J0), (name, g[name], fd)
+    flat = g["alpha"].ravel()
+    for k in range(flat.size):
+        e = np.zeros(flat.size)
+        e[k] = H_FD
+        e = e.reshape(al.shape)
+        fd = (_oracle_J(p, al + e, steps, obj) - _oracle_J(p, al - e, steps, obj)) / (2 * H_FD)
+        assert _close(flat[k], fd, J0), (k, flat[k], fd)
+
+
 @pytest.mark.parametrize("obj", [binding.LBM_ADJ_CL, binding.LBM_ADJ_FLUX])
 def test_gradient_against_fd_of_the_oracle(obj):
     al = _alpha(SMALL["N_x"])
