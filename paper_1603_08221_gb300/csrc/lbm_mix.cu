@@ -717,6 +717,32 @@ struct WallSmem {
 // DBB rule conserves each species' mass at the node whatever r is, so the
 // tau_q warps pull the wall node with r = 0 and need not wait for r (the
 // BSR rule moves mass between columns: there they evaluate r themselves).
+// One wall task of column x: r of wall `wall` (tq false) or 1/tau_q of
+// its half (tq true), from the post-collision state fin of the step about
+// to run.  Columns outside the interior get r = 1 and 1/tau_q = 1 (unused).
+template <typename ST>
+__device__ __forceinline__ void wall_task(const Lat& L, const ST* __restrict__ fin,
+                                          const float* __restrict__ alpha, const Ends& E,
+                                          const ColRef& C, int x, int wall, bool tq, float2& rv,
+                                          float& v) {
+  v = 1.0f;
+  rv = make_float2(1.0f, 1.0f);
+  if (!interior(L, x)) return;
+  const int jw = wall == 0 ? 0 : L.N - 1;
+  const float al = alpha[wall * L.Nx + x];
+  if (!tq) {
+    rv = dbb_r(L, C, fin, x, jw, al);
+  } else {
+    float fs[2][9];
+    const float2 rr = L.wall_mode == LBM_WALL_BSR ? dbb_r(L, C, fin, x, jw, al)
+                                                  : make_float2(0.0f, 0.0f);
+    pull_node(fin, L, E, C, x, jw, rr, rr, fs);
+    Macro m;
+    macro(L, C, fs, m);
+    v = 1.0f / tau_q_wall(L, m, al);
+  }
+}
+
 template <bool WITH_TQ, typename ST>
 __device__ __forceinline__ void wall_prologue(const Lat& L, const ST* __restrict__ fin,
                                               const float* __restrict__ alpha, const Ends& E,
@@ -731,27 +757,41 @@ __device__ __forceinline__ void wall_prologue(const Lat& L, const ST* __restrict
                            : (wall == 0 ? j_begin == 0 : j_end == L.N);
     float v = 1.0f;
     float2 rv = make_float2(1.0f, 1.0f);
-    if (needed && interior(L, x)) {
-      const int jw = wall == 0 ? 0 : L.N - 1;
-      const float al = alpha[wall * L.Nx + x];
-      if (!tq) {
-        rv = dbb_r(L, C, fin, x, jw, al);
-      } else {
-        float fs[2][9];
-        const float2 rr = L.wall_mode == LBM_WALL_BSR ? dbb_r(L, C, fin, x, jw, al)
-                                                      : make_float2(0.0f, 0.0f);
-        pull_node(fin, L, E, C, x, jw, rr, rr, fs);
-        Macro m;
-        macro(L, C, fs, m);
-        v = 1.0f / tau_q_wall(L, m, al);
-      }
-    }
+    if (needed) wall_task(L, fin, alpha, E, C, x, wall, tq, rv, v);
     if (tq)
       sm.om_q[wall][tx] = v;
     else
       sm.r[wall][tx] = rv;
   }
   __syncthreads();
+}
+
+// The wall tasks of every column as a kernel of their own, ahead of the
+// 16-bit step kernel: with half the bytes that step is bound by instruction
+// issue, and the prologue's barrier held its warps up (8 % of the step).
+// One thread per column and task (blockIdx.y: 0, 1 = r of the bottom, top
+// wall; 2, 3 = 1/tau_q of the bottom, top half): r_out [2][Nx] (species
+// pair), omq_out [2][Nx].
+template <typename ST>
+__global__ void __launch_bounds__(128) lbm_walls_kernel(Lat L, const ST* __restrict__ fin,
+                                                        const float* __restrict__ refrho,
+                                                        const double* __restrict__ cs_in,
+                                                        const float* __restrict__ alpha,
+                                                        float2* __restrict__ r_out,
+                                                        float* __restrict__ omq_out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= L.Nx) return;
+  const int wall = blockIdx.y & 1;
+  const bool tq = blockIdx.y >= 2;
+  const ColRef C = col_ref(L, refrho, x);
+  const Ends E = load_ends(L, cs_in, refrho);
+  float2 rv;
+  float v;
+  wall_task(L, fin, alpha, E, C, x, wall, tq, rv, v);
+  if (tq)
+    omq_out[wall * L.Nx + x] = v;
+  else
+    r_out[wall * L.Nx + x] = rv;
 }
 
 // Compensated FP32 running sum (Kahan): a thread's partial over its rows of
@@ -807,6 +847,10 @@ struct StepArgs {
   int rows_per_block;                // rows of one row block (multiple of TY)
   unsigned seed;                     // 16-bit storage: per-step seed of the
                                      // stochastic rounding; 0 = round to nearest
+  // 16-bit storage: r and 1/tau_q of every column from lbm_walls_kernel
+  // ([2][Nx] each, bottom then top), in place of the wall prologue
+  const float2* __restrict__ wall_r;
+  const float* __restrict__ wall_omq;
 };
 
 struct RedSmem {
@@ -1013,7 +1057,18 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
   // the first row of each warp is read from L2 while the wall prologue runs
   if (tx == 0 && j_begin + ty < j_end)
     prefetch_row_l2(a.fin + (size_t)blockIdx.x * L.SS + (size_t)(j_begin + ty) * RS);
-  wall_prologue<true>(L, a.fin, a.alpha, E, C, x, j_begin, j_end, wsm);
+  // r and 1/tau_q of this column: from lbm_walls_kernel (16-bit storage,
+  // read where they are used) or from the CTA's wall prologue
+  const int xc = x < L.Nx ? x : L.Nx - 1;
+  if constexpr (sizeof(ST) == 4) wall_prologue<true>(L, a.fin, a.alpha, E, C, x, j_begin, j_end, wsm);
+  auto wall_r = [&](int w) -> float2 {
+    if constexpr (sizeof(ST) < 4) return a.wall_r[w * L.Nx + xc];
+    else return wsm.r[w][tx];
+  };
+  auto wall_omq = [&](int h) -> float {
+    if constexpr (sizeof(ST) < 4) return a.wall_omq[h * L.Nx + xc];
+    else return wsm.om_q[h][tx];
+  };
   const bool in = interior(L, x);
   // strips holding column 1 or N_x - 2 take the general pull (ghost columns)
   const bool edge_strip = !L.x_periodic && (x0 <= 1 || x0 + TX > L.Nx - 2);
@@ -1022,7 +1077,6 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
   if (xp >= L.Nx) xp -= L.Nx;
   const unsigned base = blockIdx.x * L.SS + 2 * tx;  // row 0, i = 0, species a of column x
   const int offl = (int)(idx(L, 0, 0, 0, xm) - base), offr = (int)(idx(L, 0, 0, 0, xp) - base);
-  const float2 r_bot = wsm.r[0][tx], r_top = wsm.r[1][tx];
   const int half = (L.N + 1) / 2;  // rows j < half (1-based 2J <= N+1) use the bottom tau_q
   KahanF acc[4];
   const bool reduce = DIAG || edge_strip;
@@ -1042,7 +1096,7 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
         pull_fast(p, p + offl, p + offr, L, C, g);
       } else {
         float fs[2][9];
-        pull_node(a.fin, L, E, C, x, j, r_bot, r_top, fs);
+        pull_node(a.fin, L, E, C, x, j, wall_r(0), wall_r(1), fs);
 #pragma unroll
         for (int i = 0; i < 9; ++i) g[i] = make_float2(fs[0][i], fs[1][i]);
       }
@@ -1052,7 +1106,7 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
       // 16-bit storage halves the bytes and leaves the sweep bound by
       // instruction issue: there skipping psi work pays, for FP32 it does not
       rates2<(sizeof(ST) < 4)>(L, m, (float)j + 0.5f, om_s, om_d);
-      const float om_q = wsm.om_q[j < half ? 0 : 1][tx];
+      const float om_q = wall_omq(j < half ? 0 : 1);
       const float2 mxs =
           collide2(g, L, m.rho, m.ux, m.uy, L.om_e, L.om_eps, om_d, om_q, om_s);
       if (reduce) {
@@ -1333,6 +1387,8 @@ struct lbm_mix {
   double* diag;
   unsigned long long* diag_count;
   double* clprof;
+  float2* wall_r;      // [2][Nx] r per wall and column (16-bit storage)
+  float* wall_omq;     // [2][Nx] 1/tau_q per half and column (16-bit storage)
   double* colpart;     // [R][4][Nx]
   unsigned* strip_cnt; // [nblocks]
   int R, rows_per_block;
@@ -1593,6 +1649,12 @@ int launch_step(lbm_mix* h, bool diag) {
     a.seed = (sizeof(ST) < 4 && h->p.rounding == LBM_ROUND_STOCHASTIC)
                  ? (host_hash32((unsigned)(h->steps + 1)) | 1u)
                  : 0u;
+    a.wall_r = h->wall_r;
+    a.wall_omq = h->wall_omq;
+    if constexpr (sizeof(ST) < 4) {
+      lbm_walls_kernel<ST><<<dim3((h->L.Nx + 127) / 128, 4), 128, 0, h->stream>>>(
+          h->L, a.fin, h->refrho, a.cs_in, h->alpha, h->wall_r, h->wall_omq);
+    }
     dim3 blk(TX, TY), grd(h->nblocks, h->R);
     if (diag)
       lbm_step_kernel<ST, true><<<grd, blk, 0, h->stream>>>(h->L, a);
@@ -1798,6 +1860,8 @@ void lbm_mix_destroy(lbm_mix* h) {
   cudaFree(h->diag);
   cudaFree(h->diag_count);
   cudaFree(h->clprof);
+  cudaFree(h->wall_r);
+  cudaFree(h->wall_omq);
   cudaFree(h->colpart);
   cudaFree(h->strip_cnt);
   cudaFree(h->resid);
@@ -1854,6 +1918,10 @@ int lbm_mix_create(const lbm_mix_params* p, void* stream, lbm_mix** out) {
   ALLOC(h->diag, sizeof(double) * DIAG_CAP * NREC);
   ALLOC(h->diag_count, sizeof(unsigned long long));
   ALLOC(h->clprof, sizeof(double) * (size_t)Nx);
+  if (h->elem < 4) {
+    ALLOC(h->wall_r, sizeof(float2) * 2 * (size_t)Nx);
+    ALLOC(h->wall_omq, sizeof(float) * 2 * (size_t)Nx);
+  }
   // Row blocks: split each strip's rows over R CTAs of DEFAULT_ROWS rows so
   // that the grid holds many waves of CTAs on the device's SMs and its last,
   // partial wave is a small share of the launch.
@@ -2217,6 +2285,8 @@ int lbm_mix_step_noalloc(const lbm_mix_params* p, const float* d_in, float* d_ou
   a.colpart = nullptr;  // one row block per strip: no row-block partials
   a.rows_per_block = (L.N + TY - 1) / TY * TY;
   a.seed = 0u;  // FP32 storage: no rounding to 16 bits
+  a.wall_r = nullptr;  // FP32 storage: the wall prologue computes r and tau_q
+  a.wall_omq = nullptr;
   dim3 blk(TX, TY), grd(nstrips, 1);
   lbm_step_kernel<float, true><<<grd, blk, 0, s>>>(L, a);
   CK(cudaGetLastError());
