@@ -227,3 +227,30 @@ def test_round_to_nearest_is_biased(storage):
     emul = max(abs(d[0]) for (st, _, h, k), d in model.items()
                if st == name and h == 20000 and k == "CL")
     assert err > 10 * (K_MODEL * emul + FLOOR["CL"]), (err, emul)
+
+
+@pytest.mark.parametrize("case", [
+    dict(N=6, N_x=37, wall=binding.LBM_WALL_BSR),
+    dict(N=9, N_x=45, r_form=binding.LBM_R_SECOND),
+    dict(N=8, N_x=70, r_form=binding.LBM_R_SPECIES, lambda_pressure=1),
+    dict(N=10, N_x=120, C_l_out=0.3),
+])
+def test_sixteen_bit_wall_variants_follow_fp32(case):
+    """16-bit storage takes r and tau_q from a wall kernel of its own (the
+    same function the FP32 step's prologue calls).  On small ragged channels
+    with the BSR wall, the other readings of Eq. R and lambda_sigma, and
+    unequal end compositions, FP16 storage stays within 1 % of the largest
+    |u_x| of the FP32 run after 300 steps.  Wall terms taken from the wrong
+    column or half would move the near-wall flow by several per cent; FP16's
+    rounding moves it by 0.13 - 0.22 % here (GB300).  BF16, with 8x coarser
+    rounding, moves it by 1.2 - 2.0 %, too close to such an error to test."""
+    p = workloads.preset("heli_argon_320x16", theta=1.5, Kn_out=0.2, **case)
+    g32 = _run(p, 300)
+    g16 = _run(p, 300, storage=binding.LBM_FP16)
+    m32, m16 = g32.moments(), g16.moments()
+    scale = max(np.abs(m32["ua_x"]).max(), np.abs(m32["ub_x"]).max())
+    assert scale > 0
+    for k in ("ua_x", "ua_y", "ub_x", "ub_y"):
+        assert np.abs(m16[k] - m32[k]).max() < 1e-2 * scale, k
+    for k in ("rho_a", "rho_b"):
+        assert _relerr(m16[k], m32[k]) < 1e-3, k
