@@ -669,9 +669,10 @@ __device__ __forceinline__ float2 dbb_r(const Lat& L, const ColRef& C, const ST*
 
 // Density-correction factors of Eq. rho2 for the ghost columns, from the
 // column sums of the state being streamed, and the ghost reference offsets;
-// only the CTAs that own column 1 or column N_x - 2 read them.
+// only a block whose columns [x0, x0 + width) hold column 1 or column
+// N_x - 2 reads them (the others keep kappa = 1, which they never use).
 __device__ __forceinline__ Ends load_ends(const Lat& L, const double* __restrict__ cs,
-                                          const float* __restrict__ refrho) {
+                                          const float* __restrict__ refrho, int x0, int width) {
   Ends E;
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
@@ -679,17 +680,17 @@ __device__ __forceinline__ Ends load_ends(const Lat& L, const double* __restrict
     E.gin[sp] = E.gout[sp] = 0.0f;
   }
   if (L.x_periodic) return E;
-  const int Nx = L.Nx, x0 = blockIdx.x * TX;
+  const int Nx = L.Nx;
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     const double* c = cs + (size_t)sp * Nx;
     const float* r = refrho + sp * Nx;
-    if (x0 <= 1 && 1 < x0 + TX) {
+    if (x0 <= 1 && 1 < x0 + width) {
       double k = L.N * L.rho_in[sp] / (2.0 * c[1] - c[2]);
       E.kin[sp] = (float)k;
       E.gin[sp] = (float)(k * (2.0 * (double)r[1] - (double)r[2]) - (double)r[0]);
     }
-    if (x0 <= Nx - 2 && Nx - 2 < x0 + TX) {
+    if (x0 <= Nx - 2 && Nx - 2 < x0 + width) {
       double k = L.N * L.rho_out[sp] / (2.0 * c[Nx - 2] - c[Nx - 3]);
       E.kout[sp] = (float)k;
       E.gout[sp] = (float)(k * (2.0 * (double)r[Nx - 2] - (double)r[Nx - 3]) - (double)r[Nx - 1]);
@@ -784,7 +785,7 @@ __global__ void __launch_bounds__(128) lbm_walls_kernel(Lat L, const ST* __restr
   const int wall = blockIdx.y & 1;
   const bool tq = blockIdx.y >= 2;
   const ColRef C = col_ref(L, refrho, x);
-  const Ends E = load_ends(L, cs_in, refrho);
+  const Ends E = load_ends(L, cs_in, refrho, blockIdx.x * blockDim.x, blockDim.x);
   float2 rv;
   float v;
   wall_task(L, fin, alpha, E, C, x, wall, tq, rv, v);
@@ -1051,7 +1052,7 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int x0 = blockIdx.x * TX, x = x0 + tx;
   const ColRef C = col_ref(L, a.refrho, x);
-  const Ends E = load_ends(L, a.cs_in, a.refrho);
+  const Ends E = load_ends(L, a.cs_in, a.refrho, blockIdx.x * TX, TX);
   const int j_begin = blockIdx.y * a.rows_per_block;
   const int j_end = min(L.N, j_begin + a.rows_per_block);
   // the first row of each warp is read from L2 while the wall prologue runs
@@ -1151,7 +1152,7 @@ __global__ void __launch_bounds__(TX* TY)
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int x = blockIdx.x * TX + tx;
   const ColRef C = col_ref(L, refrho, x);
-  const Ends E = load_ends(L, cs_in, refrho);
+  const Ends E = load_ends(L, cs_in, refrho, blockIdx.x * TX, TX);
   if (!direct) wall_prologue<false>(L, fin, alpha, E, C, x, 0, L.N, wsm);
   if (!interior(L, x)) return;
   const size_t plane = (size_t)L.N * L.Nx;
