@@ -242,7 +242,7 @@ def test_sixteen_bit_wall_variants_follow_fp32(case):
     unequal end compositions, FP16 storage stays within 1 % of the largest
     |u_x| of the FP32 run after 300 steps.  Wall terms taken from the wrong
     column or half would move the near-wall flow by several per cent; FP16's
-    rounding moves it by 0.13 - 0.22 % here (GB300).  BF16, with 8x coarser
+    rounding moves it by 0.14 - 0.22 % here (GB300).  BF16, with 8x coarser
     rounding, moves it by 1.2 - 2.0 %, too close to such an error to test."""
     p = workloads.preset("heli_argon_320x16", theta=1.5, Kn_out=0.2, **case)
     g32 = _run(p, 300)
