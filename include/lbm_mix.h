@@ -135,7 +135,11 @@ void lbm_mix_destroy(lbm_mix* h);
 int lbm_mix_init(lbm_mix* h);
 
 /* Advances nsteps >= 0 time steps (Eq. MRT), one fused collide-stream pass
- * per step on the handle's stream, asynchronously.  The pass of every
+ * per step on the handle's stream, asynchronously.  With 16-bit storage, and
+ * with FP32 storage when the step's grid holds two or more waves of CTAs on
+ * the device, a small kernel computes r (Eq. R) and tau_q (Eq. taoq) of
+ * every column ahead of each pass; both are launched with programmatic
+ * dependent launch.  The pass of every
  * diag_every-th step (counted from init) and of the last step of the call
  * also reduces the separation diagnostics of the new state in FP64 (one
  * history record each), so lbm_mix_separation after lbm_mix_step always
@@ -246,6 +250,13 @@ int lbm_mix_get_post_state_f64(lbm_mix* h, double* f, long n);
 /* Lattice size and steps taken since init / set_post_state. */
 int lbm_mix_dims(const lbm_mix* h, int* N, int* N_x, long* steps);
 
+/* Kernel launches of one lbm_mix_step step under h's current schedule
+ * (lbm_mix_set_rows_per_block): 2 when the wall kernel runs ahead of the
+ * step kernel (16-bit storage; FP32 grids of two or more waves of CTAs),
+ * else 1; re-referencing adds its own.  Returns the count, or LBM_EINVAL
+ * for a NULL handle. */
+int lbm_mix_launches_per_step(const lbm_mix* h);
+
 /* Waits for all work enqueued on the handle's stream. */
 int lbm_mix_sync(lbm_mix* h);
 
@@ -259,8 +270,9 @@ int lbm_mix_eval_special(const double* x, double* e1, double* psi, long n);
  * cudaMalloc (for example code that owns a fixed device-memory budget that
  * is already handed out, or runs under an allocator it does not control and
  * may not bypass).  This entry point has no
- * counterpart in the paper; it runs the same fused step kernel as
- * lbm_mix_step, with the kernel's scratch (per-strip partial sums and the
+ * counterpart in the paper; it runs the fused step kernel of lbm_mix_step
+ * as one launch (r and tau_q from the kernel's own wall prologue), with the
+ * kernel's scratch (per-strip partial sums and the
  * arrival tickets of its two-level reduction) in a static device array of
  * 69 KB that every GPU loading the library holds until the process exits.
  * That array covers N_x <= 32768 columns; larger N_x is rejected with

@@ -91,6 +91,7 @@ _SIGS = {
     "lbm_mix_get_post_state": (_I, [_H, _PF, _L]),
     "lbm_mix_get_post_state_f64": (_I, [_H, _PD, _L]),
     "lbm_mix_dims": (_I, [_H, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_L)]),
+    "lbm_mix_launches_per_step": (_I, [_H]),
     "lbm_mix_sync": (_I, [_H]),
     "lbm_mix_eval_special": (_I, [_PD, _PD, _PD, _L]),
     "lbm_mix_step_noalloc": (_I, [ctypes.POINTER(lbm_mix_params)] + [ctypes.c_void_p] * 9),
@@ -205,6 +206,13 @@ def lbm_mix_dims(h):
     _check(load().lbm_mix_dims(h, ctypes.byref(N), ctypes.byref(Nx), ctypes.byref(steps)),
            "lbm_mix_dims")
     return N.value, Nx.value, steps.value
+
+
+def lbm_mix_launches_per_step(h) -> int:
+    n = load().lbm_mix_launches_per_step(h)
+    if n < 0:
+        _check(n, "lbm_mix_launches_per_step")
+    return n
 
 
 def lbm_mix_moments(h) -> dict:

@@ -333,6 +333,18 @@ __device__ __forceinline__ unsigned idx(const Lat& L, int sp, int i, int j, int 
 // contiguous RS-element run) into L2.  Issued by one lane per warp for the
 // row that warp sweeps next, so the DRAM reads of row j + TY are in flight
 // while row j is computed, with no registers or shared memory held for them.
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialisation attribute may start while the kernel before it in the
+// stream is still running.  Every kernel of the step sequence lets its
+// successor launch as soon as all of its own CTAs are running
+// (launch_dependents) and waits for its predecessor's completion and memory
+// (wait) before its first global memory access.  Launched without the
+// attribute, both instructions return at once.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <typename ST>
 __device__ __forceinline__ void prefetch_row_l2(const ST* row) {
   static_assert((RS * sizeof(ST)) % 16 == 0, "bulk prefetch size must be a multiple of 16 B");
@@ -767,9 +779,10 @@ __device__ __forceinline__ void wall_prologue(const Lat& L, const ST* __restrict
   __syncthreads();
 }
 
-// The wall tasks of every column as a kernel of their own, ahead of the
-// 16-bit step kernel: with half the bytes that step is bound by instruction
-// issue, and the prologue's barrier held its warps up (8 % of the step).
+// The wall tasks of every column as a kernel of their own, ahead of the step
+// kernel (16-bit storage, and FP32 grids of several waves): the prologue's
+// barrier held the CTA's other warps up while the tau_q warps waited on
+// their loads (8 % of the 16-bit step, 4 % of the FP32 step).
 // One thread per column and task (blockIdx.y: 0, 1 = r of the bottom, top
 // wall; 2, 3 = 1/tau_q of the bottom, top half): r_out [2][Nx] (species
 // pair), omq_out [2][Nx].
@@ -780,6 +793,8 @@ __global__ void __launch_bounds__(128) lbm_walls_kernel(Lat L, const ST* __restr
                                                         const float* __restrict__ alpha,
                                                         float2* __restrict__ r_out,
                                                         float* __restrict__ omq_out) {
+  pdl_launch_dependents();
+  pdl_wait();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= L.Nx) return;
   const int wall = blockIdx.y & 1;
@@ -848,8 +863,8 @@ struct StepArgs {
   int rows_per_block;                // rows of one row block (multiple of TY)
   unsigned seed;                     // 16-bit storage: per-step seed of the
                                      // stochastic rounding; 0 = round to nearest
-  // 16-bit storage: r and 1/tau_q of every column from lbm_walls_kernel
-  // ([2][Nx] each, bottom then top), in place of the wall prologue
+  // r and 1/tau_q of every column from lbm_walls_kernel ([2][Nx] each,
+  // bottom then top), in place of the wall prologue (WK kernels only)
   const float2* __restrict__ wall_r;
   const float* __restrict__ wall_omq;
 };
@@ -1045,10 +1060,15 @@ __device__ __forceinline__ void column_epilogue(const Lat& L, const StepArgs<ST>
 // DIAG: reduce the separation diagnostics of the new state (every
 // diag_every-th step); otherwise only the strips holding the end columns
 // reduce the column sums the next step's density correction needs.
-template <typename ST, bool DIAG>
+// WK: r and 1/tau_q of the columns come from lbm_walls_kernel, launched
+// ahead of the step (always with 16-bit storage), instead of the CTA's wall
+// prologue.
+template <typename ST, bool DIAG, bool WK = (sizeof(ST) < 4)>
 __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST> a) {
   __shared__ WallSmem wsm;
   __shared__ RedSmem rsm;
+  pdl_launch_dependents();
+  pdl_wait();
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int x0 = blockIdx.x * TX, x = x0 + tx;
   const ColRef C = col_ref(L, a.refrho, x);
@@ -1058,16 +1078,16 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
   // the first row of each warp is read from L2 while the wall prologue runs
   if (tx == 0 && j_begin + ty < j_end)
     prefetch_row_l2(a.fin + (size_t)blockIdx.x * L.SS + (size_t)(j_begin + ty) * RS);
-  // r and 1/tau_q of this column: from lbm_walls_kernel (16-bit storage,
-  // read where they are used) or from the CTA's wall prologue
+  // r and 1/tau_q of this column: from lbm_walls_kernel (WK, read where they
+  // are used) or from the CTA's wall prologue
   const int xc = x < L.Nx ? x : L.Nx - 1;
-  if constexpr (sizeof(ST) == 4) wall_prologue<true>(L, a.fin, a.alpha, E, C, x, j_begin, j_end, wsm);
+  if constexpr (!WK) wall_prologue<true>(L, a.fin, a.alpha, E, C, x, j_begin, j_end, wsm);
   auto wall_r = [&](int w) -> float2 {
-    if constexpr (sizeof(ST) < 4) return a.wall_r[w * L.Nx + xc];
+    if constexpr (WK) return a.wall_r[w * L.Nx + xc];
     else return wsm.r[w][tx];
   };
   auto wall_omq = [&](int h) -> float {
-    if constexpr (sizeof(ST) < 4) return a.wall_omq[h * L.Nx + xc];
+    if constexpr (WK) return a.wall_omq[h * L.Nx + xc];
     else return wsm.om_q[h][tx];
   };
   const bool in = interior(L, x);
@@ -1388,8 +1408,8 @@ struct lbm_mix {
   double* diag;
   unsigned long long* diag_count;
   double* clprof;
-  float2* wall_r;      // [2][Nx] r per wall and column (16-bit storage)
-  float* wall_omq;     // [2][Nx] 1/tau_q per half and column (16-bit storage)
+  float2* wall_r;      // [2][Nx] r per wall and column (lbm_walls_kernel)
+  float* wall_omq;     // [2][Nx] 1/tau_q per half and column (lbm_walls_kernel)
   double* colpart;     // [R][4][Nx]
   unsigned* strip_cnt; // [nblocks]
   int R, rows_per_block;
@@ -1627,6 +1647,18 @@ int reset_diag(lbm_mix* h) {
   return LBM_OK;
 }
 
+// FP32 storage takes r and tau_q from lbm_walls_kernel when the step's grid
+// holds at least WALL_KERNEL_WAVES waves of resident CTAs (3 per SM): there
+// the CTA prologue's barrier costs more than a launch of its own (0.400
+// against 0.406 ms on the 32768 x 512 channel).  A grid of a wave or less,
+// like the channels of a parametric sweep, keeps the prologue, which costs
+// less than the extra launch.  16-bit storage always uses the wall kernel.
+constexpr long WALL_KERNEL_WAVES = 2;
+bool uses_wall_kernel(const lbm_mix* h) {
+  const long ctas = (long)h->nblocks * (long)h->R;
+  return ctas >= WALL_KERNEL_WAVES * 3L * (long)(h->nsm > 0 ? h->nsm : 1);
+}
+
 int launch_step(lbm_mix* h, bool diag) {
   const int b = h->cur;
   int st = with_storage(h, [&](auto tag) -> int {
@@ -1652,16 +1684,37 @@ int launch_step(lbm_mix* h, bool diag) {
                  : 0u;
     a.wall_r = h->wall_r;
     a.wall_omq = h->wall_omq;
-    if constexpr (sizeof(ST) < 4) {
-      lbm_walls_kernel<ST><<<dim3((h->L.Nx + 127) / 128, 4), 128, 0, h->stream>>>(
-          h->L, a.fin, h->refrho, a.cs_in, h->alpha, h->wall_r, h->wall_omq);
+    // Both kernels are launched with programmatic stream serialisation, so
+    // that each one's launch and CTA ramp overlap the end of the kernel
+    // before it (see pdl_wait).
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.stream = h->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const bool wk = sizeof(ST) < 4 || uses_wall_kernel(h);
+    if (wk) {
+      cfg.gridDim = dim3((h->L.Nx + 127) / 128, 4);
+      cfg.blockDim = dim3(128);
+      CK(cudaLaunchKernelEx(&cfg, lbm_walls_kernel<ST>, h->L, a.fin, (const float*)h->refrho,
+                            (const double*)a.cs_in, (const float*)h->alpha, h->wall_r,
+                            h->wall_omq));
     }
-    dim3 blk(TX, TY), grd(h->nblocks, h->R);
-    if (diag)
-      lbm_step_kernel<ST, true><<<grd, blk, 0, h->stream>>>(h->L, a);
-    else
-      lbm_step_kernel<ST, false><<<grd, blk, 0, h->stream>>>(h->L, a);
-    CK(cudaGetLastError());
+    cfg.gridDim = dim3(h->nblocks, h->R);
+    cfg.blockDim = dim3(TX, TY);
+    if (sizeof(ST) < 4 || !wk) {
+      if (diag)
+        CK(cudaLaunchKernelEx(&cfg, lbm_step_kernel<ST, true>, h->L, a));
+      else
+        CK(cudaLaunchKernelEx(&cfg, lbm_step_kernel<ST, false>, h->L, a));
+    } else {
+      if (diag)
+        CK(cudaLaunchKernelEx(&cfg, lbm_step_kernel<ST, true, true>, h->L, a));
+      else
+        CK(cudaLaunchKernelEx(&cfg, lbm_step_kernel<ST, false, true>, h->L, a));
+    }
     return LBM_OK;
   });
   if (st) return st;
@@ -1919,10 +1972,8 @@ int lbm_mix_create(const lbm_mix_params* p, void* stream, lbm_mix** out) {
   ALLOC(h->diag, sizeof(double) * DIAG_CAP * NREC);
   ALLOC(h->diag_count, sizeof(unsigned long long));
   ALLOC(h->clprof, sizeof(double) * (size_t)Nx);
-  if (h->elem < 4) {
-    ALLOC(h->wall_r, sizeof(float2) * 2 * (size_t)Nx);
-    ALLOC(h->wall_omq, sizeof(float) * 2 * (size_t)Nx);
-  }
+  ALLOC(h->wall_r, sizeof(float2) * 2 * (size_t)Nx);
+  ALLOC(h->wall_omq, sizeof(float) * 2 * (size_t)Nx);
   // Row blocks: split each strip's rows over R CTAs of DEFAULT_ROWS rows so
   // that the grid holds many waves of CTAs on the device's SMs and its last,
   // partial wave is a small share of the launch.
@@ -2210,6 +2261,12 @@ int lbm_mix_dims(const lbm_mix* h, int* N, int* N_x, long* steps) {
   if (N_x) *N_x = h->L.Nx;
   if (steps) *steps = h->steps;
   return LBM_OK;
+}
+
+int lbm_mix_launches_per_step(const lbm_mix* h) {
+  int st = check_handle(h);
+  if (st) return st;
+  return (h->elem < 4 || uses_wall_kernel(h)) ? 2 : 1;
 }
 
 int lbm_mix_sync(lbm_mix* h) {

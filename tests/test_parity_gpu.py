@@ -406,3 +406,39 @@ def test_alternative_readings(reading):
     _check_moments(g, o)
     sg, so = g.separation(), o.separation()
     assert abs(sg["CL"] - so["CL"]) < 1e-3 * max(abs(so["CL"]), 1e-4)
+
+
+@pytest.mark.parametrize("reading", [dict(), dict(wall=binding.LBM_WALL_BSR,
+                                                  r_form=binding.LBM_R_SPECIES, C_l_out=0.3)])
+def test_wall_kernel_and_wall_prologue(reading):
+    """An FP32 step whose grid holds two or more waves of CTAs (3 per SM)
+    takes r and tau_q from the separate wall kernel; a smaller grid computes
+    them in each CTA's prologue.  One channel run both ways, 8-row blocks
+    (8 CTAs per strip: the wall kernel) and one row block per strip (the
+    prologue), each against the oracle and against each other, where only
+    the order of the FP64 column sums differs."""
+    import torch
+
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    strips = -(-2 * 3 * nsm // 8)
+    assert strips < 2 * 3 * nsm  # one row block per strip stays under two waves
+    p = workloads.preset("heli_argon_320x16", N=64, N_x=32 * strips - 5, theta=1.5, **reading)
+    alpha = workloads.random_accommodation(p["N_x"], seed=3, spread=0.05)
+    o = oracle.Oracle(p)
+    o.init()
+    o.set_accommodation_field(alpha)
+    o.step(120)
+    runs = []
+    for rows in (8, 64):
+        g = binding.LbmMix(**p)
+        g.set_rows_per_block(rows)
+        g.init()
+        g.set_accommodation_field(alpha)
+        g.step(120)
+        mg, _ = _check_moments(g, o)
+        sg, so = g.separation(), o.separation()
+        assert abs(sg["CL"] - so["CL"]) < 1e-6 + 1e-3 * abs(so["CL"])
+        assert abs(sg["mdot_a"] / so["mdot_a"] - 1) < RTOL_U
+        runs.append(mg)
+    for k in ("rho_a", "rho_b", "ua_x", "ub_x"):
+        assert _relerr(runs[0][k], runs[1][k]) < 1e-6, k
