@@ -47,6 +47,14 @@
 
 namespace {
 
+// Programmatic dependent launch of the per-step kernel sequences: each
+// kernel lets the next one in its stream launch once all of its own CTAs
+// run (launch_dependents), and waits for the previous one's completion and
+// memory (wait) before its first global memory access, so that launches
+// and CTA ramps overlap the end of the kernel before.  Both return at once
+// for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 constexpr double kPiD = 3.14159265358979323846;
 constexpr double kEulerGamma = 0.57721566490153286061;
 // D2Q9 velocities c_i = (cxd(i), cyd(i)) (Eq. c).  Compile-time functions,
@@ -713,6 +721,7 @@ __device__ double block_sum256(double v, double* sm /* [8] */) {
 // species.
 __global__ void __launch_bounds__(256) adj_kappa_kernel(AL L, const double* __restrict__ f,
                                                         double* __restrict__ kap) {
+  pdl_enter();
   __shared__ double sm[8];
   const int t = threadIdx.x, e = blockIdx.x, sp = e & 1;
   const int x1 = e < 2 ? 1 : L.Nx - 2, x2 = e < 2 ? 2 : L.Nx - 3;
@@ -738,6 +747,7 @@ __global__ void __launch_bounds__(256) adj_kappa_kernel(AL L, const double* __re
 // (c.dr, for the reverse of the DBB rule).
 __global__ void adj_cols_kernel(AL L, const double* __restrict__ f, const double* __restrict__ alpha,
                                 StepCols c) {
+  pdl_enter();
   const int x = blockIdx.x * blockDim.x + threadIdx.x, w = blockIdx.y;
   if (x >= L.Nx) return;
   const size_t k = (size_t)w * L.Nx + x, wn = 2 * (size_t)L.Nx;
@@ -758,6 +768,7 @@ __global__ void adj_cols_kernel(AL L, const double* __restrict__ f, const double
 // lanes at once, so a thread per wall node is the cheap layout.
 __global__ void adj_tauq_kernel(AL L, const double* __restrict__ f, const double* __restrict__ alpha,
                                 StepCols c) {
+  pdl_enter();
   const int x = blockIdx.x * blockDim.x + threadIdx.x, w = blockIdx.y;
   if (x >= L.Nx || !interior(L, x)) return;
   double g[2][9];
@@ -788,6 +799,7 @@ __global__ void adj_tauq_kernel(AL L, const double* __restrict__ f, const double
 __global__ void __launch_bounds__(32, 19) adj_step_kernel(AL L, const double* __restrict__ fin,
                                                       double* __restrict__ fout, StepCols c,
                                                       double* __restrict__ psi_out, int rows) {
+  pdl_enter();
   const int x = blockIdx.x * 32 + threadIdx.x;
   if (x >= L.Nx || !interior(L, x)) return;
   const int j0 = blockIdx.y * rows, j1 = min(L.N, j0 + rows);
@@ -886,6 +898,7 @@ __global__ void __launch_bounds__(32) adj_rev_node_kernel(
     AL L, const double* __restrict__ fin, const double* __restrict__ lam, StepCols c,
     const double* __restrict__ psi, int rows, double* __restrict__ gbar,
     double* __restrict__ part) {
+  pdl_enter();
   const int x = blockIdx.x * 32 + threadIdx.x;
   if (x >= L.Nx || !interior(L, x)) return;
   const int j0 = blockIdx.y * rows, j1 = min(L.N, j0 + rows);
@@ -931,6 +944,7 @@ constexpr int kRevTauqWarps = 4;
 __global__ void __launch_bounds__(32 * kRevTauqWarps) adj_rev_tauq_kernel(
     AL L, StepCols c, const double* __restrict__ part, double* __restrict__ gbar,
     double* __restrict__ alphabar, double* __restrict__ lnmu_col) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   const int item = blockIdx.x * kRevTauqWarps + (threadIdx.x >> 5);
   if (item >= 2 * L.Nx) return;  // warp-uniform
@@ -972,6 +986,7 @@ __global__ void __launch_bounds__(32 * kRevTauqWarps) adj_rev_tauq_kernel(
 __global__ void __launch_bounds__(128) adj_rev_pull_kernel(
     AL L, const double* __restrict__ fin, StepCols c, const double* __restrict__ gbar,
     const double* __restrict__ gk, double* __restrict__ lamp, double* __restrict__ alphabar) {
+  pdl_enter();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (x >= L.Nx) return;
@@ -1063,6 +1078,7 @@ __global__ void __launch_bounds__(128) adj_rev_pull_kernel(
 __global__ void __launch_bounds__(256) adj_rev_kappa_kernel(
     AL L, const double* __restrict__ fin, StepCols c, const double* __restrict__ gbar,
     double* __restrict__ gk, double* __restrict__ theta_acc) {
+  pdl_enter();
   __shared__ double sm[8];
   const int t = threadIdx.x, e = blockIdx.x;
   if (L.x_periodic) return;
@@ -1224,19 +1240,35 @@ cudaError_t node_rows(const void* kernel, int Nx, int N, int* rows) {
   return cudaSuccess;
 }
 
+// Launches kern with programmatic stream serialisation (see pdl_enter).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Forward step from f (input) into fo, column data into cols, on stream st.
 int fwd_step(lbm_adj* a, const double* f, double* fo, StepCols c, cudaStream_t st,
              double* psi_out = nullptr) {
   const AL& L = a->L;
-  adj_kappa_kernel<<<4, 256, 0, st>>>(L, f, c.kappa);
+  CKA(launch_pdl(adj_kappa_kernel, dim3(4), dim3(256), st, L, f, c.kappa));
   // one thread per (column, wall): small blocks spread the FP64 work of
   // the wall columns over many SMs
   const dim3 wg((L.Nx + 31) / 32, 2);
-  adj_cols_kernel<<<wg, 32, 0, st>>>(L, f, a->alpha, c);
-  adj_tauq_kernel<<<wg, 32, 0, st>>>(L, f, a->alpha, c);
-  adj_step_kernel<<<dim3((L.Nx + 31) / 32, (L.N + a->rows_step - 1) / a->rows_step), 32, 0, st>>>(
-      L, f, fo, c, psi_out, a->rows_step);
-  CKA(cudaGetLastError());
+  CKA(launch_pdl(adj_cols_kernel, wg, dim3(32), st, L, f, (const double*)a->alpha, c));
+  CKA(launch_pdl(adj_tauq_kernel, wg, dim3(32), st, L, f, (const double*)a->alpha, c));
+  CKA(launch_pdl(adj_step_kernel,
+                 dim3((L.Nx + 31) / 32, (L.N + a->rows_step - 1) / a->rows_step), dim3(32), st,
+                 L, f, fo, c, psi_out, a->rows_step));
   return LBM_OK;
 }
 
@@ -1525,18 +1557,19 @@ int lbm_adj_gradient(lbm_adj* a, int objective, double* dtheta, double* dkn, dou
       const long k = t - t0 - 1;
       const double* fin = a->seg[b] + a->S * (size_t)k;
       StepCols c = cols_of(a, a->segcols[b] + cw * k);
-      adj_rev_node_kernel<<<dim3((L.Nx + 31) / 32, (L.N + a->rows_rev - 1) / a->rows_rev), 32, 0,
-                            a->stream>>>(L, fin, a->lam[cur], c,
-                                         a->segpsi[b] + psi_step * (size_t)k, a->rows_rev,
-                                         a->gbar, a->part_rev);
-      adj_rev_tauq_kernel<<<(2 * L.Nx + kRevTauqWarps - 1) / kRevTauqWarps, 32 * kRevTauqWarps,
-                            0, a->stream>>>(
-          L, c, a->part_rev, a->gbar, a->alphabar, a->lnmu_col);
+      CKA(launch_pdl(adj_rev_node_kernel,
+                     dim3((L.Nx + 31) / 32, (L.N + a->rows_rev - 1) / a->rows_rev), dim3(32),
+                     a->stream, L, fin, (const double*)a->lam[cur], c,
+                     (const double*)(a->segpsi[b] + psi_step * (size_t)k), a->rows_rev, a->gbar,
+                     a->part_rev));
+      CKA(launch_pdl(adj_rev_tauq_kernel, dim3((2 * L.Nx + kRevTauqWarps - 1) / kRevTauqWarps),
+                     dim3(32 * kRevTauqWarps), a->stream, L, c, (const double*)a->part_rev,
+                     a->gbar, a->alphabar, a->lnmu_col));
       // one block per (end, species); the pull adds its kappa terms
-      adj_rev_kappa_kernel<<<4, 256, 0, a->stream>>>(L, fin, c, a->gbar, a->gk, a->theta_acc);
-      adj_rev_pull_kernel<<<grd, 128, 0, a->stream>>>(L, fin, c, a->gbar, a->gk, a->lam[1 - cur],
-                                                      a->alphabar);
-      CKA(cudaGetLastError());
+      CKA(launch_pdl(adj_rev_kappa_kernel, dim3(4), dim3(256), a->stream, L, fin, c,
+                     (const double*)a->gbar, a->gk, a->theta_acc));
+      CKA(launch_pdl(adj_rev_pull_kernel, grd, dim3(128), a->stream, L, fin, c,
+                     (const double*)a->gbar, (const double*)a->gk, a->lam[1 - cur], a->alphabar));
       cur = 1 - cur;
     }
     CKA(cudaEventRecord(a->ev_rev[b], a->stream));
