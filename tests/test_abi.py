@@ -73,6 +73,7 @@ def test_null_arguments(lib):
     assert lib.lbm_mix_create(None, None, ctypes.byref(h)) == binding.LBM_EINVAL
     assert lib.lbm_mix_step(None, 1) == binding.LBM_EINVAL
     assert lib.lbm_mix_init(None) == binding.LBM_EINVAL
+    assert lib.lbm_mix_launches_per_step(None) == binding.LBM_EINVAL
     lib.lbm_mix_destroy(None)  # NULL-safe
 
 

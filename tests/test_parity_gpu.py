@@ -432,6 +432,7 @@ def test_wall_kernel_and_wall_prologue(reading):
     for rows in (8, 64):
         g = binding.LbmMix(**p)
         g.set_rows_per_block(rows)
+        assert binding.lbm_mix_launches_per_step(g.h) == (2 if rows == 8 else 1)
         g.init()
         g.set_accommodation_field(alpha)
         g.step(120)
