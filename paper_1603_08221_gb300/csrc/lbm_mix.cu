@@ -329,10 +329,6 @@ __device__ __forceinline__ unsigned idx(const Lat& L, int sp, int i, int j, int 
   return (unsigned)(x >> 5) * L.SS + (unsigned)(j * RS + i * PS + 2 * (x & 31) + sp);
 }
 
-// Bulk prefetch of one strip row (all 18 populations of 32 columns, one
-// contiguous RS-element run) into L2.  Issued by one lane per warp for the
-// row that warp sweeps next, so the DRAM reads of row j + TY are in flight
-// while row j is computed, with no registers or shared memory held for them.
 // Programmatic dependent launch: a kernel launched with the programmatic
 // stream-serialisation attribute may start while the kernel before it in the
 // stream is still running.  The kernels of the step sequence wait for their
@@ -347,6 +343,10 @@ __device__ __forceinline__ void pdl_launch_dependents() {
 }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Bulk prefetch of one strip row (all 18 populations of 32 columns, one
+// contiguous RS-element run) into L2.  Issued by one lane per warp for the
+// row that warp sweeps next, so the DRAM reads of row j + TY are in flight
+// while row j is computed, with no registers or shared memory held for them.
 template <typename ST>
 __device__ __forceinline__ void prefetch_row_l2(const ST* row) {
   static_assert((RS * sizeof(ST)) % 16 == 0, "bulk prefetch size must be a multiple of 16 B");
