@@ -34,6 +34,7 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (the roofline uses the measured
 WORKLOAD = "neon_argon_32768x512"
 REF_SAMPLE = "neon_argon_2048x32"  # 1/16 linear-scale copy (same C_l, theta, Kn_out)
 KERNEL = "lbm_step_kernel"
+TUNE_STEPS = 50  # timed steps per candidate schedule of lbm_mix_tune_rows
 PROFILE_MD = os.path.join(ROOT, "profiles", "lbm_step_kernel_neon_argon_32768x512.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_1603_08221_gb300", "csrc", "lbm_mix.cu")
 KERNEL_SECTION_END = b"// ------------------------------------------------------------ init kernels"
@@ -379,7 +380,15 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     sim = binding.LbmMix(stream=stream, storage=storage, **p)
     nodes = sim.N * (sim.N_x - 2)
+    # schedule: rows per CTA timed over real steps (untimed setup), then the
+    # run starts again from the initial state
     sim.init()
+    if args.rows > 0:
+        sim.set_rows_per_block(args.rows)
+        rows = args.rows
+    else:
+        rows = sim.tune_rows(steps=TUNE_STEPS)
+        sim.init()
 
     def barrier():
         if world > 1:
@@ -435,6 +444,12 @@ def run_ours(args):
         for name, storage in (("bf16", binding.LBM_BF16), ("fp16", binding.LBM_FP16)):
             v = binding.LbmMix(stream=stream, storage=storage, **p)
             v.init()
+            if args.rows > 0:
+                v.set_rows_per_block(args.rows)
+                v_rows = args.rows
+            else:
+                v_rows = v.tune_rows(steps=TUNE_STEPS)
+                v.init()
             binding.lbm_mix_step(v.h, args.warmup)
             barrier()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -447,7 +462,7 @@ def run_ours(args):
             variants[name] = {"ms_per_step": t_v * 1e3, "value": nodes / t_v / 1e6,
                               "unit": "MLUPS", "bytes_per_node_step": BYTES_PER_NODE // 2,
                               "achieved_gbs": BYTES_PER_NODE // 2 * nodes / t_v / 1e9,
-                              "reref_every": 256}
+                              "reref_every": 256, "rows_per_block": v_rows}
             del v
 
     sweep = None if args.no_sweep else run_sweep(args, rank, world, barrier)
@@ -495,6 +510,10 @@ def run_ours(args):
                    "Kn_out": p["Kn_out"], "nodes_updated": nodes,
                    "bytes_per_node_step": bytes_per_node, "storage": args.storage,
                    "diag_every": args.diag_every,
+                   "rows_per_block": rows,
+                   "schedule": ("given (--rows)" if args.rows > 0 else
+                                f"rows per CTA tuned over {TUNE_STEPS} steps per candidate "
+                                "(lbm_mix_tune_rows) before init; not timed"),
                    "l2": "state (2 x 1.2 GB FP32) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -529,6 +548,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--rows", type=int, default=0,
+                    help="rows per CTA of the step kernel; 0 = tune (lbm_mix_tune_rows)")
     ap.add_argument("--storage", choices=["fp32", "bf16", "fp16"], default="fp32",
                     help="population storage of the timed channel (FP32 is the headline)")
     ap.add_argument("--cpu-steps", type=int, default=2000,

@@ -322,6 +322,20 @@ int lbm_mix_step_noalloc(const lbm_mix_params* p, const float* d_in, float* d_ou
  * LBM_ECUDA. */
 int lbm_mix_set_rows_per_block(lbm_mix* h, int rows);
 
+/* Picks the node-to-CTA schedule of h by timing real steps: for each of the
+ * n candidate row counts (multiples of 8; candidates = NULL takes 64, 72,
+ * 80, 88, 96, 112 and 128) it runs 2 untimed steps and `steps` steps timed
+ * with CUDA events on the handle's stream, then keeps the fastest (ties to
+ * the earlier candidate) and writes it to *best_rows (NULL-safe).  Which
+ * count is fastest depends on how the grid's CTAs fill the device's waves,
+ * so it differs between channel sizes and storage types.  The steps advance
+ * the state (n * (steps + 2) of them, with their diagnostic records):
+ * call lbm_mix_init or lbm_mix_set_post_state afterwards to start a run
+ * from a chosen state.  Synchronises.  Not during stream capture.
+ * Errors: LBM_EINVAL (bad handle, candidates or steps), LBM_ENOMEM,
+ * LBM_ECUDA, and any error of lbm_mix_step. */
+int lbm_mix_tune_rows(lbm_mix* h, const int* candidates, int n, long steps, int* best_rows);
+
 /* ---------------------------------------------------------------------
  * Parametric sweeps (the study of Table 1 and Sec. 4: many independent
  * channels).  No counterpart in the paper's method: a batching device.

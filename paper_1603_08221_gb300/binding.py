@@ -96,6 +96,7 @@ _SIGS = {
     "lbm_mix_eval_special": (_I, [_PD, _PD, _PD, _L]),
     "lbm_mix_step_noalloc": (_I, [ctypes.POINTER(lbm_mix_params)] + [ctypes.c_void_p] * 9),
     "lbm_mix_set_rows_per_block": (_I, [_H, _I]),
+    "lbm_mix_tune_rows": (_I, [_H, ctypes.POINTER(_I), _I, _L, ctypes.POINTER(_I)]),
     "lbm_sweep_create": (_I, [ctypes.POINTER(lbm_mix_params), _I,
                               ctypes.POINTER(ctypes.c_void_p)]),
     "lbm_sweep_destroy": (None, [_H]),
@@ -352,6 +353,20 @@ def lbm_mix_set_rows_per_block(h, rows: int) -> None:
     _check(load().lbm_mix_set_rows_per_block(h, int(rows)), "lbm_mix_set_rows_per_block")
 
 
+def lbm_mix_tune_rows(h, candidates=None, steps: int = 20) -> int:
+    """Times `steps` real steps under each candidate rows-per-CTA (None: the
+    library's list) and keeps the fastest; returns it.  Advances the state."""
+    best = _I()
+    if candidates is None:
+        arr, n = None, 0
+    else:
+        arr = (_I * len(candidates))(*[int(c) for c in candidates])
+        n = len(candidates)
+    _check(load().lbm_mix_tune_rows(h, arr, n, int(steps), ctypes.byref(best)),
+           "lbm_mix_tune_rows")
+    return best.value
+
+
 LBM_SWEEP_NPOLICY = 5
 
 
@@ -427,6 +442,9 @@ class LbmMix:
 
     def set_rows_per_block(self, rows: int):
         lbm_mix_set_rows_per_block(self.h, rows)
+
+    def tune_rows(self, candidates=None, steps: int = 20) -> int:
+        return lbm_mix_tune_rows(self.h, candidates, steps)
 
     def __del__(self):
         try:

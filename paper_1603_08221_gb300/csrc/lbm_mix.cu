@@ -2121,6 +2121,50 @@ int lbm_mix_set_rows_per_block(lbm_mix* h, int rows) {
   return set_rows_per_block(h, rows);
 }
 
+int lbm_mix_tune_rows(lbm_mix* h, const int* candidates, int n, long steps, int* best_rows) {
+  int st = check_handle(h);
+  if (st) return st;
+  static const int kDefault[] = {64, 72, 80, 88, 96, 112, 128};
+  if (!candidates) {
+    candidates = kDefault;
+    n = (int)(sizeof kDefault / sizeof kDefault[0]);
+  }
+  if (n < 1 || steps < 1) return set_err(LBM_EINVAL, "need n >= 1 candidates and steps >= 1");
+  for (int k = 0; k < n; ++k)
+    if (candidates[k] <= 0 || candidates[k] % TY != 0)
+      return set_err(LBM_EINVAL, "candidate %d: rows must be a positive multiple of %d", k, TY);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return set_err(LBM_ECUDA, "cudaEventCreate failed");
+  }
+  int best = h->rows_per_block;
+  float best_ms = INFINITY;
+  for (int k = 0; k < n && st == LBM_OK; ++k) {
+    if ((st = set_rows_per_block(h, candidates[k]))) break;
+    // two untimed steps settle the new schedule (first-touch of its buffers)
+    if ((st = lbm_mix_step(h, 2))) break;
+    if (cudaEventRecord(e0, h->stream) != cudaSuccess ||
+        (st = lbm_mix_step(h, steps)) != LBM_OK || cudaEventRecord(e1, h->stream) != cudaSuccess ||
+        cudaEventSynchronize(e1) != cudaSuccess) {
+      if (st == LBM_OK) st = set_err(LBM_ECUDA, "timing a candidate schedule failed");
+      break;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = h->rows_per_block;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) return st;
+  if ((st = set_rows_per_block(h, best))) return st;
+  if (best_rows) *best_rows = best;
+  return LBM_OK;
+}
+
 int lbm_mix_moments_device(lbm_mix* h, double* d_out) {
   int st = check_handle(h);
   if (st) return st;

@@ -74,6 +74,7 @@ def test_null_arguments(lib):
     assert lib.lbm_mix_step(None, 1) == binding.LBM_EINVAL
     assert lib.lbm_mix_init(None) == binding.LBM_EINVAL
     assert lib.lbm_mix_launches_per_step(None) == binding.LBM_EINVAL
+    assert lib.lbm_mix_tune_rows(None, None, 0, 10, None) == binding.LBM_EINVAL
     lib.lbm_mix_destroy(None)  # NULL-safe
 
 

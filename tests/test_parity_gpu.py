@@ -443,3 +443,24 @@ def test_wall_kernel_and_wall_prologue(reading):
         runs.append(mg)
     for k in ("rho_a", "rho_b", "ua_x", "ub_x"):
         assert _relerr(runs[0][k], runs[1][k]) < 1e-6, k
+
+
+def test_tuned_schedule():
+    """lbm_mix_tune_rows times real steps under each candidate rows per CTA
+    and keeps one of them; a run from the initial state under the chosen
+    schedule still matches the oracle.  Bad candidates are rejected."""
+    p = workloads.preset("neon_argon_2048x32", N=20, N_x=100, theta=1.5)
+    g = binding.LbmMix(**p)
+    g.init()
+    best = g.tune_rows([8, 16, 24], steps=3)
+    assert best in (8, 16, 24)
+    with pytest.raises(binding.LbmError):
+        g.tune_rows([8, 12], steps=3)
+    with pytest.raises(binding.LbmError):
+        g.tune_rows([8], steps=0)
+    g.init()
+    g.step(300)
+    o = oracle.Oracle(p)
+    o.init()
+    o.step(300)
+    _check_moments(g, o)
