@@ -12,9 +12,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_prints_one_contract_line():
+    # a small workload keeps the CPU suite short; the default is the full channel
     out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "3",
-                          "--warmup", "3"], cwd=ROOT, capture_output=True, text=True,
-                         timeout=600)
+                          "--warmup", "3", "--workload", "neon_argon_2048x32"], cwd=ROOT,
+                         capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr
     lines = [l for l in out.stdout.splitlines() if l.strip()]
     assert len(lines) == 1
@@ -25,6 +26,8 @@ def test_reference_arm_prints_one_contract_line():
     assert rec["impl"] == "reference" and rec["metric"] == "MLUPS" and rec["value"] > 0
     assert rec["cpu_baseline"]["kind"] == "oracle" and rec["cpu_baseline"]["cores"] >= 1
     assert rec["e2e"]["h2d_bytes_per_step"] == 0 and rec["e2e"]["value"] == rec["value"]
+    assert rec["config"]["workload"] == "neon_argon_2048x32"
+    assert rec["config"]["nodes_updated"] == 32 * (2048 - 2)
 
 
 def test_profile_summary_traffic_is_current():
