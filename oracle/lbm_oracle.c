@@ -51,7 +51,11 @@
  * parity unpinned: the absolute values of CL, C~_l and the velocity profiles
  * cannot be compared with the paper (its figures are not available and c_m,
  * mu_s are not given); the tests pin this file against invariants, closed
- * forms and independent special cases instead.
+ * forms and independent special cases instead.  In tau_q_of, the last term
+ * of Eq. taoq (its 12 and 30) is pinned only through the closed form of
+ * tau'_s(0): it vanishes at uniform tau_s, where the slip-law pins are
+ * exact, and elsewhere changes the slip only at O(dx^2), which the
+ * convergence of the discrete channel does not resolve.
  */
 #include <math.h>
 #include <stdint.h>
