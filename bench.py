@@ -427,6 +427,8 @@ def run_ours(args):
     # more waves), per step; 16-bit storage adds, every 256 steps (counted
     # from the handle's first step), the two kernels of a re-reference
     per_step = binding.lbm_mix_launches_per_step(sim.h)
+    # bytes of one population buffer (strips of 32 columns, 18 values per node)
+    state_gb = 18 * sim.N * 32 * ((sim.N_x + 31) // 32) * (4 if args.storage == "fp32" else 2) / 1e9
     launches = args.steps * per_step
     if args.storage != "fp32":
         launches += 2 * ((args.warmup + args.steps) // 256 - args.warmup // 256)
@@ -533,7 +535,9 @@ def run_ours(args):
                    "schedule": ("given (--rows)" if args.rows > 0 else
                                 f"rows per CTA tuned over {TUNE_STEPS} steps per candidate "
                                 "(lbm_mix_tune_rows) before init; not timed"),
-                   "l2": "state (2 x 1.2 GB FP32) larger than L2; no flush",
+                   "l2": (f"state (2 x {state_gb:.2f} GB {args.storage.upper()}) larger "
+                          "than L2; no flush" if state_gb > 0.129 else
+                          f"state (2 x {state_gb:.3f} GB) fits in L2: not a DRAM figure"),
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
