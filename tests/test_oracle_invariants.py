@@ -262,8 +262,9 @@ _OPEN_READINGS = (
     "under every reading tried of what the paper leaves open (r_sigma of Eq. R in "
     "its two printed forms and with m_sigma for m_min; lambda_sigma with the partial "
     "or the mixture pressure) CL moves the other way, here and for every Table 1 run "
-    "on the paper's 700 x 20 lattice (oracle and GPU agree); mu_sigma and c_m are not "
-    "given by the paper")
+    "on the paper's 700 x 20 lattice (oracle and GPU agree), and under species "
+    "viscosity ratios 0.25 ... 1 and slip coefficients c_m0 0.5 ... 2, which the paper "
+    "does not give")
 
 
 @pytest.mark.xfail(strict=True, reason="Sec. 4.1 / Conclusions: CL falls as theta grows; "
