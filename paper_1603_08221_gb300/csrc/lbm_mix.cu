@@ -1,8 +1,10 @@
 // lbm_mix.cu — sm_103a implementation of the C ABI in include/lbm_mix.h.
 //
 // One time step of the two-species D2Q9 MRT lattice Boltzmann model of
-// Wang, Xu & Guo (arXiv:1603.08221, Sec. 3) is ONE kernel launch
-// (lbm_step_kernel): pull-streaming from the previous post-collision buffer
+// Wang, Xu & Guo (arXiv:1603.08221, Sec. 3) is ONE fused kernel launch
+// (lbm_step_kernel; on grids of two or more waves and with 16-bit storage,
+// lbm_walls_kernel computes the wall parameters r and tau_q of every column
+// ahead of it): pull-streaming from the previous post-collision buffer
 // with the diffuse-bounce-back walls (Eqs. bot, bot2, R) and the
 // extrapolation-correction ends (Eqs. rho1, rho2) folded into the loads,
 // moments (Eq. rhou), effective relaxation times (Eqs. EQFrb, EQFrsp, psi,
