@@ -1082,7 +1082,8 @@ __global__ void __launch_bounds__(TX* TY, 3) lbm_step_kernel(Lat L, StepArgs<ST>
   const Ends E = load_ends(L, a.cs_in, a.refrho, blockIdx.x * TX, TX);
   const int j_begin = blockIdx.y * a.rows_per_block;
   const int j_end = min(L.N, j_begin + a.rows_per_block);
-  // the first row of each warp is read from L2 while the wall prologue runs
+  // the first row of each warp is on its way into L2 while the wall prologue
+  // (if any) runs
   if (tx == 0 && j_begin + ty < j_end)
     prefetch_row_l2(a.fin + (size_t)blockIdx.x * L.SS + (size_t)(j_begin + ty) * RS);
   // r and 1/tau_q of this column: from lbm_walls_kernel (WK, read where they
