@@ -295,11 +295,15 @@ def test_neon_argon_2048x32_2000_steps():
 
 def test_neon_argon_full_size_one_step():
     """The 32768 x 512 throughput workload in the launch configuration the
-    benchmark times: after 3 GPU steps, the oracle takes the GPU's
+    benchmark times (the rows per CTA lbm_mix_tune_rows picks, the wall
+    kernel ahead of the step): after 3 GPU steps, the oracle takes the GPU's
     post-collision state and advances it one step; every node's moments of
     that step must match the GPU's."""
     p = workloads.preset("neon_argon_32768x512")
     g = binding.LbmMix(**p)
+    g.init()
+    g.tune_rows(steps=5)
+    assert binding.lbm_mix_launches_per_step(g.h) == 2
     g.init()
     g.step(3)
     fp = g.get_post_state_f64()
