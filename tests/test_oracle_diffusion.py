@@ -1,0 +1,91 @@
+"""Interdiffusion of the oracle against the kinetic theory of hard spheres:
+a pin of Eq. EQFrsp (the diffusion relaxation time tau_d) and of the species
+mean free paths it is built from, for unequal masses and compositions.
+
+A small sinusoidal wave of the mole fraction x_a on a uniform-pressure,
+periodic box (no walls, Psi = 1) decays as exp(-D k^2 t).  The decay rate
+measured from the oracle's time steps gives the scheme's interdiffusion
+coefficient D without reference to any formula for it.
+
+The reference is the first Chapman-Enskog approximation for rigid spheres:
+    D_ab = (3/16) sqrt(2 pi k_B T / m_r) / (n pi d_ab^2),
+m_r = m_a m_b/(m_a + m_b), d_ab = (d_a + d_b)/2, with each diameter taken
+from the species' viscosity, mu_s = (5/16) sqrt(m_s k_B T / pi) / d_s^2
+(the viscosities mu_s the oracle was given).
+
+What ties the two: at uniform pressure the tau_d relaxation of the species
+momenta towards rho_s u gives, to first order, rho_s (u_s - u) =
+-(tau_d - 1/2) p grad x_s, whose number flux relative to the mean number
+velocity is Fick's law with D = (tau_d - 1/2) k_B T m_x / (m_a m_b).  With
+tau_d of Eq. EQFrsp and lambda_s = (mu_s / p_s) sqrt(pi k_B T / (2 m_s))
+(partial pressure), m_x cancels and D = (5 sqrt(pi) / 16) D_ab for every
+mass ratio and composition.  The test asserts that constant ratio.
+
+On scratch copies of the oracle, plausible mistakes in Eq. EQFrsp moved the
+ratio far outside the 2.5e-3 bound (measured 8e-4 for the true formula at
+L = 128, the lattice's O(k^2) error): m_x instead of m_x^2 (up to 170 %),
+m_0 = m_a m_b instead of m_a + m_b (29 %), 1.4 for the 3/2 (6.6 %),
+lambda_s / x_s for x_s lambda_s (400 %), m_a^2 for m_a m_b (68 %).  The
+other reading of lambda_s, with the mixture pressure (lambda_pressure = 1),
+gives a ratio 50 to 61 % below the constant: rigid-sphere theory sides with
+the partial pressure, the default reading.
+"""
+import math
+
+import numpy as np
+import pytest
+
+RATIO = 5.0 * math.sqrt(math.pi) / 16.0
+KT = 1.0 / 3.0  # lattice units, masses in units of m_min
+
+
+def _measured_and_kinetic_D(orc, m_a, m_b, x0, Kn, L=128, eps=0.01, steps=3000, every=100):
+    light_is_a = m_a < m_b
+    p = dict(m_a=m_a, m_b=m_b, C_l=x0 if light_is_a else 1.0 - x0, theta=1.0, Kn_out=Kn,
+             N=2, N_x=L, x_periodic=1, y_periodic=1, psi_off=1)
+    o = orc.Oracle(p)
+    c = o.constants()
+    mh = np.array([c["mh_a"], c["mh_b"]])
+    s = np.array([c["s_a"], c["s_b"]])
+    k = 2.0 * math.pi / L
+    x = np.arange(L)
+    xa = x0 + eps * np.sin(k * x)
+    f = np.zeros((2, 9, 2, L))
+    for sp, frac in ((0, xa), (1, 1.0 - xa)):  # n = 1 everywhere: uniform pressure
+        for ix in range(L):
+            f[sp, :, :, ix] = orc.feq(frac[ix] * mh[sp], s[sp], 0.0, 0.0)[:, None]
+    o.set_post_state(f)
+    ts, amps = [], []
+    for t in range(0, steps + 1, every):
+        if t:
+            o.step(every)
+        m = o.moments()
+        na, nb = m["rho_a"][0] / mh[0], m["rho_b"][0] / mh[1]
+        xt = na / (na + nb)
+        amps.append(2.0 / L * np.sum((xt - xt.mean()) * np.sin(k * x)))
+        ts.append(t)
+    ts, amps = np.array(ts), np.array(amps)
+    late = ts >= steps // 3  # after the acoustic transient
+    rate = -np.polyfit(ts[late], np.log(np.abs(amps[late])), 1)[0]
+    D_meas = rate / k**2
+    # rigid spheres with the oracle's species viscosities, number density 1
+    n = 1.0
+    d = [math.sqrt(5.0 / 16.0 * math.sqrt(mh[sp] * KT / math.pi) / c["mu_" + "ab"[sp]])
+         for sp in (0, 1)]
+    d_ab = 0.5 * (d[0] + d[1])
+    m_r = mh[0] * mh[1] / (mh[0] + mh[1])
+    D_hs = 3.0 / 16.0 * math.sqrt(2.0 * math.pi * KT / m_r) / (n * math.pi * d_ab**2)
+    return D_meas, D_hs
+
+
+@pytest.mark.parametrize("m_a,m_b,x0,Kn", [
+    (4.003, 39.948, 0.3, 0.05),   # He-Ar, light-poor
+    (4.003, 39.948, 0.7, 0.05),   # He-Ar, light-rich
+    (20.18, 39.948, 0.5, 0.05),   # Ne-Ar
+    (39.948, 4.003, 0.5, 0.05),   # species order swapped
+    (10.0, 10.0, 0.5, 0.05),      # identical species (self-diffusion)
+    (4.003, 39.948, 0.5, 0.2),    # four times the mean free paths
+])
+def test_interdiffusion_is_hard_sphere_kinetic_theory(orc, m_a, m_b, x0, Kn):
+    D_meas, D_hs = _measured_and_kinetic_D(orc, m_a, m_b, x0, Kn)
+    assert abs(D_meas / D_hs / RATIO - 1.0) < 2.5e-3, (D_meas, D_hs, D_meas / D_hs)
