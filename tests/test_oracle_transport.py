@@ -1,6 +1,8 @@
-"""Interdiffusion of the oracle against the kinetic theory of hard spheres:
-a pin of Eq. EQFrsp (the diffusion relaxation time tau_d) and of the species
-mean free paths it is built from, for unequal masses and compositions.
+"""Transport coefficients of the oracle measured from its own time steps:
+the shear viscosity against the imposed mu (Eqs. EQFrb, taos), and the
+interdiffusion coefficient against the kinetic theory of hard spheres (a pin
+of Eq. EQFrsp, the diffusion relaxation time tau_d, and of the species mean
+free paths it is built from), for unequal masses and compositions.
 
 A small sinusoidal wave of the mole fraction x_a on a uniform-pressure,
 periodic box (no walls, Psi = 1) decays as exp(-D k^2 t).  The decay rate
@@ -22,8 +24,8 @@ tau_d of Eq. EQFrsp and lambda_s = (mu_s / p_s) sqrt(pi k_B T / (2 m_s))
 mass ratio and composition.  The test asserts that constant ratio.
 
 On scratch copies of the oracle, plausible mistakes in Eq. EQFrsp moved the
-ratio far outside the 2.5e-3 bound (measured 8e-4 for the true formula at
-L = 128, the lattice's O(k^2) error): m_x instead of m_x^2 (up to 170 %),
+ratio far outside the 2.5e-3 bound (measured 4e-4 ... 1.3e-3 for the true
+formula at L = 128, the lattice's O(k^2) error): m_x instead of m_x^2 (up to 170 %),
 m_0 = m_a m_b instead of m_a + m_b (29 %), 1.4 for the 3/2 (6.6 %),
 lambda_s / x_s for x_s lambda_s (400 %), m_a^2 for m_a m_b (68 %).  The
 other reading of lambda_s, with the mixture pressure (lambda_pressure = 1),
@@ -89,3 +91,55 @@ def _measured_and_kinetic_D(orc, m_a, m_b, x0, Kn, L=128, eps=0.01, steps=3000, 
 def test_interdiffusion_is_hard_sphere_kinetic_theory(orc, m_a, m_b, x0, Kn):
     D_meas, D_hs = _measured_and_kinetic_D(orc, m_a, m_b, x0, Kn)
     assert abs(D_meas / D_hs / RATIO - 1.0) < 2.5e-3, (D_meas, D_hs, D_meas / D_hs)
+
+
+def _measured_viscosity(orc, m_a, m_b, x0, Kn, L=128, eps=1e-4, steps=2000, every=50):
+    """mu = rho nu from the decay exp(-nu k^2 t) of a transverse velocity wave
+    u_y = eps sin(k x) at uniform composition and pressure."""
+    p = dict(m_a=m_a, m_b=m_b, C_l=x0 if m_a < m_b else 1.0 - x0, theta=1.0, Kn_out=Kn,
+             N=2, N_x=L, x_periodic=1, y_periodic=1, psi_off=1)
+    o = orc.Oracle(p)
+    c = o.constants()
+    mh = np.array([c["mh_a"], c["mh_b"]])
+    s = np.array([c["s_a"], c["s_b"]])
+    k = 2.0 * math.pi / L
+    x = np.arange(L)
+    uy = eps * np.sin(k * x)
+    f = np.zeros((2, 9, 2, L))
+    for sp, frac in ((0, x0), (1, 1.0 - x0)):
+        for ix in range(L):
+            f[sp, :, :, ix] = orc.feq(frac * mh[sp], s[sp], 0.0, uy[ix])[:, None]
+    o.set_post_state(f)
+    ts, amps = [], []
+    for t in range(0, steps + 1, every):
+        if t:
+            o.step(every)
+        m = o.moments()
+        rho = m["rho_a"][0] + m["rho_b"][0]
+        u = (m["rho_a"][0] * m["ua_y"][0] + m["rho_b"][0] * m["ub_y"][0]) / rho
+        amps.append(2.0 / L * np.sum(u * np.sin(k * x)))
+        ts.append(t)
+    ts, amps = np.array(ts), np.array(amps)
+    late = ts >= steps // 4
+    rate = -np.polyfit(ts[late], np.log(np.abs(amps[late])), 1)[0]
+    rho0 = x0 * mh[0] + (1.0 - x0) * mh[1]
+    return rate / k**2 * rho0, c["mu"]
+
+
+@pytest.mark.parametrize("m_a,m_b,x0,Kn", [
+    (4.003, 39.948, 0.3, 0.05),
+    (4.003, 39.948, 0.7, 0.05),
+    (20.18, 39.948, 0.5, 0.05),
+    (39.948, 4.003, 0.5, 0.05),
+    (4.003, 39.948, 0.5, 0.2),
+])
+def test_shear_viscosity_is_the_imposed_viscosity(orc, m_a, m_b, x0, Kn):
+    """The mixture's shear viscosity, measured from a decaying shear wave,
+    equals the viscosity mu the run was set up with (measured within 1e-4):
+    tau_s of Eq. taos from lambda = (mu/p) sqrt(pi k_B T/(2 m_x)) (Eq. EQFrb's
+    mean free path) gives rho c_s^2 (tau_s - 1/2) = mu whatever the masses
+    and composition.  On scratch copies of the oracle, tau_s without its
+    m_x, or lambda with m_min in place of m_x, put He-Ar off by 92 ... 170 %,
+    and a 3 for the 2 in lambda by 18 %."""
+    mu_meas, mu = _measured_viscosity(orc, m_a, m_b, x0, Kn)
+    assert abs(mu_meas / mu - 1.0) < 1e-3, (mu_meas, mu)
